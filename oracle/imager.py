@@ -1,0 +1,415 @@
+"""FP64 CPU oracle of the bounded least-squares imager.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU-baseline / reference legs of ``bench.py`` may import or run this
+module.  The product path (the CUDA library and its Python binding) never
+calls it and shares no code with it.
+
+Everything is plain numpy/scipy in float64 / complex128, written to be read
+against the paper (Sardarabadi, Leshem, van der Veen, "Radio astronomical
+image formation using constrained least squares and Krylov subspaces"):
+
+* steering vectors, Sec. II and Sec. IV-D steering model, unit norm;
+* the Khatri-Rao operator Psi = conj(A) o A built column by column
+  (Sec. III-A, eq. bAt; properties listed in Sec. I notation);
+* matched-filter dirty image, eq. mfdimg;
+* MVDR bound with bias constant C and variances, eq. wmvdr, eq. UBMVDRV,
+  eq. D and Appendix A;
+* CLS (eq. CLS) and preconditioned WLS (eq. preWLS) costs, gradients
+  eq. gls / eq. gmvdr;
+* the active-set method of Table I with the step of eq. mumax;
+* LSQR (Paige & Saunders 1982, referenced in Sec. V-A) on the
+  Golub-Kahan recurrences eq. initbeta .. eq. lanczos.
+
+Readings where the paper is silent or ambiguous (documented beside each use):
+steering sign -j; K = 1 snapshot; detection threshold eps_i = kappa * std_i
+with a relative floor; ties resolved to the smallest pixel index; cold-start
+LSQR; non-strict feasibility.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.linalg as sla
+
+COST_LS = 0
+COST_PWLS = 1
+BOUND_MF = 0
+BOUND_MVDR = 1
+INFLATE_NONE = 0
+INFLATE_RATIO = 1     # gamma = (1 + alpha) * dirty              (Sec. III-D)
+INFLATE_STD = 2       # gamma = dirty + alpha * std(dirty)        (Appendix A)
+
+SET_L, SET_U, SET_F = 0, 1, 2
+
+
+# ---------------------------------------------------------------- Sec. II
+def pixel_directions(l: np.ndarray, m: np.ndarray):
+    """Pixel i = i_l + n_l * i_m (column-major vect of the image)."""
+    n_l = l.shape[0]
+    Q = n_l * m.shape[0]
+    idx = np.arange(Q)
+    ll = l[idx % n_l]
+    mm = m[idx // n_l]
+    nn = np.sqrt(np.maximum(0.0, 1.0 - ll * ll - mm * mm))
+    return ll, mm, nn
+
+
+def steering_matrix(ant_xyz: np.ndarray, l: np.ndarray, m: np.ndarray,
+                    lam: float) -> np.ndarray:
+    """A (p x Q): a_i = p^{-1/2} exp(-j 2 pi <x_k, s_i> / lam).
+
+    Sec. IV-D gives the model with +j; the sign is a convention that only
+    conjugates every covariance, and -j is used on both the data and the
+    imaging side.  Normalisation a_i^H a_i = 1 (Sec. III-A)."""
+    p = ant_xyz.shape[0]
+    ll, mm, nn = pixel_directions(l, m)
+    phase = -2.0 * np.pi * (np.outer(ant_xyz[:, 0], ll) + np.outer(ant_xyz[:, 1], mm)
+                            + np.outer(ant_xyz[:, 2], nn)) / lam
+    return np.exp(1j * phase) / math.sqrt(p)
+
+
+def vect(X: np.ndarray) -> np.ndarray:
+    """Column stacking (notation section)."""
+    return X.reshape(-1, order="F")
+
+
+def unvect(x: np.ndarray, p: int) -> np.ndarray:
+    return x.reshape(p, p, order="F")
+
+
+# ---------------------------------------------------------------- Sec. III
+def khatri_rao_psi(A: np.ndarray) -> np.ndarray:
+    """Psi = conj(A) o A (eq. bAt with K = 1): column i is kron(conj(a_i), a_i),
+    which equals vect(a_i a_i^H)."""
+    p, Q = A.shape
+    Psi = np.empty((p * p, Q), dtype=np.complex128)
+    for i in range(Q):
+        Psi[:, i] = np.kron(A[:, i].conj(), A[:, i])
+    return Psi
+
+
+def dirty_mf(Psi: np.ndarray, R: np.ndarray) -> np.ndarray:
+    """Matched-filter dirty image, eq. mfdimg: (1/K) Psi^H r_hat, K = 1."""
+    return np.real(Psi.conj().T @ vect(R))
+
+
+def cholesky_lower(R: np.ndarray) -> np.ndarray:
+    """R = L L^H (raises numpy.linalg.LinAlgError when R is not PD)."""
+    return np.linalg.cholesky(R)
+
+
+def mvdr_h(A: np.ndarray, R: np.ndarray) -> np.ndarray:
+    """h_i = a_i^H R^{-1} a_i via the Cholesky factor: ||L^{-1} a_i||^2."""
+    Lc = cholesky_lower(R)
+    B = sla.solve_triangular(Lc, A, lower=True)
+    return np.sum(np.abs(B) ** 2, axis=0)
+
+
+def bias_constant(N: int, p: int, bias_c: int) -> float:
+    """C = N/(N-p) (Appendix A, eq. C) when requested, else 1."""
+    return float(N) / float(N - p) if bias_c else 1.0
+
+
+@dataclass
+class Bounds:
+    dirty: np.ndarray        # MF dirty image sigma_MF
+    h: np.ndarray            # a_i^H R^{-1} a_i
+    mvdr: np.ndarray         # C / h  (eq. wmvdr with K=1, bias-corrected form)
+    D: np.ndarray            # h^2 / C  (eq. D, K = 1)
+    std_mf: np.ndarray       # sqrt(Var(sigma_MF)) (Appendix A)
+    std_mvdr: np.ndarray     # sqrt(Var(sigma_MVDR)) (Appendix A)
+    gamma: np.ndarray        # upper bound actually used, in sigma units
+    eps: np.ndarray          # detection threshold for the chosen cost
+    C: float
+
+
+@dataclass
+class Params:
+    cost: int = COST_PWLS
+    bound: int = BOUND_MVDR
+    bias_c: int = 0
+    inflate: int = INFLATE_NONE
+    alpha: float = 6.0
+    kappa: float = 6.0
+    eps_floor: float = 1e-12     # eps_i >= eps_floor * max(dirty image of the cost)
+    lsqr_atol: float = 1e-12
+    lsqr_btol: float = 1e-12
+    lsqr_maxit: int = 0          # 0 -> 4 f + 20
+    max_outer: int = 0           # 0 -> 10 Q + 100 passes of the Table I loop
+
+
+def bounds(A: np.ndarray, Psi: np.ndarray, R: np.ndarray, N: int,
+           prm: Params) -> Bounds:
+    """Dirty images, upper bounds, preconditioner D and thresholds.
+
+    * sigma_MF = Psi^H vect(R)                      eq. mfdimg
+    * sigma_MVDR = C / (a^H R^{-1} a)               Sec. III-D (unbiased MVDR, K=1)
+    * D = (1/(K C)) diag^2(A^H R^{-1} A)            eq. D
+    * Var(sigma_MF,i) = (a^H R a)^2 / N             Appendix A (K=1, R -> R_hat)
+    * Var(sigma_MVDR,i) = sigma_MVDR,i^2 / (N-p-1)  Appendix A (K=1, with the
+      unbiased estimate h/C plugged in for a^H R^{-1} a)
+    * gamma: the chosen dirty image, optionally inflated (Sec. III-D or
+      Appendix A);  eps_i = kappa * std_i of the cost's dirty image (Sec. IV-C)."""
+    p = A.shape[0]
+    dirty = dirty_mf(Psi, R)
+    h = mvdr_h(A, R)
+    C = bias_constant(N, p, prm.bias_c)
+    mv = C / h
+    D = h * h / C
+    std_mf = dirty / math.sqrt(N)
+    dof = N - p - 1
+    std_mv = mv / math.sqrt(dof) if dof > 0 else np.full_like(mv, np.inf)
+    if prm.bound == BOUND_MF:
+        base, sd = dirty, std_mf
+    else:
+        base, sd = mv, std_mv
+    if prm.inflate == INFLATE_RATIO:
+        gamma = (1.0 + prm.alpha) * base
+    elif prm.inflate == INFLATE_STD:
+        gamma = base + prm.alpha * sd
+    else:
+        gamma = base.copy()
+    if prm.cost == COST_LS:
+        eps = prm.kappa * std_mf
+        eps = np.maximum(eps, prm.eps_floor * float(np.max(dirty)))
+    else:
+        eps = prm.kappa * std_mv
+        eps = np.maximum(eps, prm.eps_floor * float(np.max(mv)))
+    return Bounds(dirty, h, mv, D, std_mf, std_mv, gamma, eps, C)
+
+
+# ---------------------------------------------------------------- cost operators
+@dataclass
+class CostProblem:
+    """min 1/2 ||b - M x||^2 s.t. 0 <= x <= upper (eq. CLS or eq. preWLS).
+
+    CLS:  M = Psi,             b = vect(R),        x = sigma,    upper = gamma.
+    PWLS: M = W Psi D^{-1},    b = W vect(R),      x = D sigma,  upper = D gamma,
+          with W = conj(L^{-1}) kron L^{-1}.  W replaces R^{-T/2} kron R^{-1/2}:
+          ||W y|| = ||(R^{-T/2} kron R^{-1/2}) y|| for every y because
+          W^H W = R^{-T} kron R^{-1}, so cost, gradient and optimum coincide.
+    ``to_sigma`` maps the solver variable back to the image (sigma = D^{-1} x)."""
+    M: np.ndarray
+    b: np.ndarray
+    upper: np.ndarray
+    to_sigma: np.ndarray
+
+
+def cost_problem(A: np.ndarray, Psi: np.ndarray, R: np.ndarray, bnd: Bounds,
+                 cost: int) -> CostProblem:
+    p = R.shape[0]
+    if cost == COST_LS:
+        return CostProblem(Psi, vect(R).astype(np.complex128), bnd.gamma.copy(),
+                           np.ones_like(bnd.gamma))
+    Lc = cholesky_lower(R)
+    Linv = sla.solve_triangular(Lc, np.eye(p, dtype=np.complex128), lower=True)
+    # W Psi = (conj(L^-1) kron L^-1)(conj(A) o A) = conj(L^-1 A) o (L^-1 A): the
+    # mixed-product rule for Khatri-Rao products (notation section).  The
+    # explicit Kronecker route is checked against this one in the tests.
+    M = khatri_rao_psi(Linv @ A) / bnd.D[None, :]
+    b = vect(Linv @ R @ Linv.conj().T)           # W vect(R) = vect(L^-1 R L^-H)
+    return CostProblem(M, b, bnd.D * bnd.gamma, 1.0 / bnd.D)
+
+
+def gradient(prob: CostProblem, x: np.ndarray) -> np.ndarray:
+    """g(x) = -M^H (b - M x), eq. gWLS specialised in eq. gls / eq. gmvdr
+    (K = 1).  M^H of a vectorised Hermitian matrix is real; the real part is
+    taken explicitly."""
+    r = prob.b - prob.M @ x
+    return -np.real(prob.M.conj().T @ r)
+
+
+# ---------------------------------------------------------------- Sec. V-A
+@dataclass
+class LsqrResult:
+    x: np.ndarray
+    iters: int
+    istop: int
+    rnorm: float
+    arnorm: float
+
+
+def lsqr(M: np.ndarray, b: np.ndarray, atol: float, btol: float,
+         maxit: int) -> LsqrResult:
+    """LSQR for min ||b - M x|| over REAL x with complex M and b.
+
+    The u-space is C^{p^2} with the real inner product Re<.,.>; since b and
+    every M v are vectorised Hermitian matrices, M^H u is real and the real
+    part is taken explicitly.  Bidiagonalisation: eq. initbeta, eq. initu and
+    eq. lanczos.  Solution update and stopping rules follow Paige & Saunders
+    (1982), cited for the scalar steps in Sec. V-A:
+      istop 1: ||r|| <= btol ||b|| + atol ||M|| ||x||
+      istop 2: ||M^H r|| <= atol ||M|| ||r||
+      istop 3: iteration limit.
+    Cold start x0 = 0 (eq. initbeta)."""
+    n = M.shape[1]
+    x = np.zeros(n)
+    if n == 0:
+        return LsqrResult(x, 0, 0, float(np.linalg.norm(b)), 0.0)
+    beta = float(np.linalg.norm(b))
+    bnorm = beta
+    if beta == 0.0:
+        return LsqrResult(x, 0, 0, 0.0, 0.0)
+    u = b / beta
+    v = np.real(M.conj().T @ u)
+    alpha = float(np.linalg.norm(v))
+    if alpha == 0.0:
+        return LsqrResult(x, 0, 2, beta, 0.0)
+    v = v / alpha
+    w = v.copy()
+    phibar, rhobar = beta, alpha
+    anorm2 = 0.0
+    rnorm, arnorm = beta, alpha * beta
+    istop, it = 3, 0
+    for it in range(1, maxit + 1):
+        # Golub-Kahan step, eq. lanczos
+        u = M @ v - alpha * u
+        beta = float(np.linalg.norm(u))
+        if beta > 0.0:
+            u = u / beta
+        anorm2 += alpha * alpha + beta * beta
+        v = np.real(M.conj().T @ u) - beta * v
+        alpha = float(np.linalg.norm(v))
+        if alpha > 0.0:
+            v = v / alpha
+        # plane rotation eliminating the subdiagonal beta of B
+        rho = math.hypot(rhobar, beta)
+        c = rhobar / rho
+        s = beta / rho
+        theta = s * alpha
+        rhobar = -c * alpha
+        phi = c * phibar
+        phibar = s * phibar
+        x = x + (phi / rho) * w
+        w = v - (theta / rho) * w
+        rnorm = phibar
+        arnorm = phibar * alpha * abs(c)
+        anorm = math.sqrt(anorm2)
+        xnorm = float(np.linalg.norm(x))
+        if rnorm <= btol * bnorm + atol * anorm * xnorm:
+            istop = 1
+            break
+        if arnorm <= atol * anorm * rnorm:
+            istop = 2
+            break
+    return LsqrResult(x, it, istop, rnorm, arnorm)
+
+
+# ---------------------------------------------------------------- Table I
+@dataclass
+class SolveResult:
+    sigma: np.ndarray          # image (sigma units)
+    x: np.ndarray              # solver variable (sigma or D sigma)
+    sets: np.ndarray           # per pixel SET_L / SET_U / SET_F
+    outer: int                 # loop passes of Table I
+    lsqr_iters: int
+    converged: bool
+    events: list = field(default_factory=list)   # ('free', i) / ('clamp', i, set)
+    grad: np.ndarray | None = None               # last full gradient
+
+
+def active_set(prob: CostProblem, eps: np.ndarray, prm: Params,
+               record: bool = True) -> SolveResult:
+    """Active-set method of Table I for min 1/2||b - Mx||^2, 0 <= x <= upper.
+
+    Start x = 0, all pixels in L, F empty, flag Freegradient-isnotzero = True.
+    While flag or a multiplier is below its threshold:
+      if flag: z = argmin over x_F of the equality subproblem
+               (eq. subproblemLS / eq. subproblemMVDR, b_sub = b - M_U x_U);
+               if z feasible: x_F = z, flag = False, gradient on the active
+               set, lambda_L = g_L, lambda_U = -g_U (eq. etaL / eq. etaU);
+               else: p = z - x_F, mu_i from eq. mumax, step mu_max, move the
+               pixel that reaches its bound to L or U, flag = True.
+      else:    move i_min from the active set to F, flag = True.
+    Detection (Sec. IV-C): candidates are i in A with lambda_i < -eps_i; the
+    candidate with the smallest lambda_i is freed, ties to the smallest index.
+    mu ties go to the smallest pixel index; p_i = 0 gives mu_i = +inf.
+    Feasibility is non-strict: 0 <= z_i <= upper_i."""
+    M, b, up = prob.M, prob.b, prob.upper
+    Q = M.shape[1]
+    x = np.zeros(Q)
+    sets = np.full(Q, SET_L, dtype=np.int8)
+    flag = True
+    i_min = -1
+    outer = 0
+    lsqr_total = 0
+    events = []
+    max_outer = prm.max_outer if prm.max_outer > 0 else 10 * Q + 100
+    g = None
+    converged = False
+    while outer < max_outer:
+        outer += 1
+        if flag:
+            F = np.nonzero(sets == SET_F)[0]
+            U = np.nonzero(sets == SET_U)[0]
+            if F.size:
+                b_sub = b - M[:, U] @ x[U]
+                maxit = prm.lsqr_maxit if prm.lsqr_maxit > 0 else 4 * F.size + 20
+                res = lsqr(M[:, F], b_sub, prm.lsqr_atol, prm.lsqr_btol, maxit)
+                lsqr_total += res.iters
+                z = res.x
+            else:
+                z = np.zeros(0)
+            feasible = bool(np.all(z >= 0.0) and np.all(z <= up[F]))
+            if feasible:
+                x[F] = z
+                flag = False
+                g = gradient(prob, x)
+                lam = np.where(sets == SET_U, -g, g)
+                cand = (sets != SET_F) & (lam < -eps)
+                if not np.any(cand):
+                    converged = True
+                    break
+                lam_c = np.where(cand, lam, np.inf)
+                i_min = int(np.argmin(lam_c))          # first index on ties
+            else:
+                pdir = z - x[F]
+                mu = np.full(F.size, np.inf)
+                pos = pdir > 0
+                neg = pdir < 0
+                mu[pos] = (up[F][pos] - x[F][pos]) / pdir[pos]
+                mu[neg] = -x[F][neg] / pdir[neg]
+                k = int(np.argmin(mu))                 # F is sorted: smallest index
+                mu_max = float(mu[k])
+                x[F] = x[F] + mu_max * pdir
+                i = int(F[k])
+                if pdir[k] > 0:
+                    sets[i] = SET_U
+                    x[i] = up[i]
+                else:
+                    sets[i] = SET_L
+                    x[i] = 0.0
+                if record:
+                    events.append(("clamp", i, int(sets[i])))
+                flag = True
+        else:
+            sets[i_min] = SET_F
+            if record:
+                events.append(("free", i_min))
+            flag = True
+    return SolveResult(prob.to_sigma * x, x, sets, outer, lsqr_total, converged,
+                       events, g)
+
+
+# ---------------------------------------------------------------- one image
+@dataclass
+class ImageResult:
+    bounds: Bounds
+    solve: SolveResult
+
+
+def image(ant_xyz, l, m, lam, R, N, prm: Params) -> ImageResult:
+    """Full pipeline for one job: bounds, then the bounded LS solve."""
+    A = steering_matrix(ant_xyz, l, m, lam)
+    Psi = khatri_rao_psi(A)
+    bnd = bounds(A, Psi, R, N, prm)
+    prob = cost_problem(A, Psi, R, bnd, prm.cost)
+    res = active_set(prob, bnd.eps, prm)
+    return ImageResult(bnd, res)
+
+
+def image_job(job, prm: Params) -> ImageResult:
+    return image(job.ant_xyz, job.l, job.m, job.lam, job.R, job.N, prm)
