@@ -1,0 +1,190 @@
+/*
+ * img.h - C ABI of the GB300 bounded least-squares radio imager.
+ *
+ * The library estimates a sky image sigma (one real power per pixel) from an
+ * array covariance matrix R_hat, following Sardarabadi, Leshem & van der Veen,
+ * "Radio astronomical image formation using constrained least squares and
+ * Krylov subspaces":
+ *
+ *   min_sigma 1/2 || W (r_hat - Psi sigma) ||^2   s.t.  0 <= sigma <= gamma
+ *
+ * with Psi = conj(A) o A the Khatri-Rao operator of the steering matrix A
+ * (Sec. III-A, eq. bAt), W = I for constrained LS (eq. CLS) or the whitening
+ * conj(L^-1) kron L^-1 with R_hat = L L^H plus the Jacobi change of variable
+ * D for preconditioned WLS (eq. preWLS), and gamma the matched-filter or MVDR
+ * dirty image (Sec. III-D).  The active-set method of Table I decides which
+ * pixels are free; each equality subproblem is solved by LSQR (Sec. V-A) on
+ * the operator pair Psi v = vect(A diag(v) A^H) and
+ * Psi^H u = vectdiag(A^H U A) (Sec. V-B), never storing Psi or A.
+ *
+ * All work runs in CUDA kernels on one GPU; there is no CPU fallback.  A
+ * missing or unusable GPU makes img_create return IMG_ECUDA.
+ *
+ * Conventions for every entry point
+ *   - Matrices are column-major.  Complex numbers are interleaved (re, im)
+ *     pairs of float (IMG_C64) or double (IMG_C128).
+ *   - Pixel i = i_l + n_l * i_m  (column-major vectorisation of the image).
+ *   - `on_device` = 0: the pointer is host memory (pageable or pinned).
+ *     `on_device` = 1: the pointer is device memory of the context's device.
+ *   - The caller owns every buffer it passes; the library copies what it
+ *     keeps and never frees caller memory.
+ *   - Calls on one context are not thread-safe; separate contexts are
+ *     independent.  Every call returns after its results are in the
+ *     caller's buffer (it synchronises the context's stream).
+ *   - No C++ exception crosses this boundary; failures are status codes.
+ */
+#ifndef IMG_GB300_H
+#define IMG_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct img_ctx img_ctx;
+
+typedef enum {
+    IMG_OK = 0,
+    IMG_EINVAL = 1,     /* bad argument or call order                        */
+    IMG_ENOMEM = 2,     /* device allocation failed or a capacity exceeded   */
+    IMG_ENOTPD = 3,     /* R_hat is not positive definite (Cholesky failed)  */
+    IMG_ENOTCONV = 4,   /* active-set loop hit max_outer; partial image kept */
+    IMG_ETIMEOUT = 5,   /* a bounded device wait ran out                     */
+    IMG_ECUDA = 6       /* CUDA runtime error (no device, launch failure)    */
+} img_status;
+
+enum { IMG_COST_LS = 0, IMG_COST_PWLS = 1 };           /* eq. CLS / eq. preWLS   */
+enum { IMG_BOUND_MF = 0, IMG_BOUND_MVDR = 1 };         /* eq. mfupper / mvdr_upper */
+enum { IMG_INFLATE_NONE = 0,                           /* gamma = dirty          */
+       IMG_INFLATE_RATIO = 1,                          /* (1 + alpha) dirty      */
+       IMG_INFLATE_STD = 2 };                          /* dirty + alpha std      */
+enum { IMG_C64 = 0, IMG_C128 = 1 };
+enum { IMG_PREC_FP32 = 0,       /* FP32 operators on CUDA cores              */
+       IMG_PREC_TF32X3 = 1,     /* split TF32 tensor-core operators          */
+       IMG_PREC_BF16X3 = 2 };   /* split BF16 tensor-core operators          */
+enum { IMG_SET_L = 0, IMG_SET_U = 1, IMG_SET_F = 2 };  /* pixel sets (Sec. IV-A) */
+
+/*
+ * Problem description.  img_create copies every field and array.
+ *   p        antennas, 2 <= p <= 512
+ *   n_l,n_m  grid size, Q = n_l * n_m <= 2^24
+ *   ant_xyz  host, p x 3 row-major (x_k, y_k, z_k) in units of the reference
+ *            wavelength.  z_k must be 0 (planar array): the separable
+ *            steering tables need it.  Non-zero z gives IMG_EINVAL.
+ *   l, m     host, direction cosines of the grid lines (n_l and n_m values)
+ *   lambda   wavelength in reference units (> 0); phases are x_k l / lambda
+ *   Steering vector (Sec. II, Sec. IV-D, unit norm, sign -j):
+ *     a_{k,i} = p^{-1/2} exp(-j 2 pi (x_k l_{i_l} + y_k m_{i_m}) / lambda)
+ *   cost     IMG_COST_LS or IMG_COST_PWLS
+ *   bound    IMG_BOUND_MF or IMG_BOUND_MVDR
+ *   bias_c   0: C = 1;  1: C = N / (N - p)       (Appendix A, eq. C)
+ *   inflate, alpha   upper-bound inflation (Sec. III-D and Appendix A)
+ *   kappa    detection threshold eps_i = kappa * std_i of the cost's dirty
+ *            image (Sec. IV-C); 0 asks for the exact KKT point
+ *   eps_floor  eps_i >= eps_floor * max(dirty image of the cost)
+ *   lsqr_atol, lsqr_btol, lsqr_maxit  LSQR stopping rules (Paige-Saunders);
+ *            maxit 0 means 4 f + 20 for f free pixels
+ *   max_outer  cap on passes of the Table I loop (0: 10 Q + 100)
+ *   precision  IMG_PREC_*
+ *   support_cap  most pixels allowed off the lower bound at once (|F u U|);
+ *            0 means min(Q, 16384).  Exceeding it ends the solve with
+ *            IMG_ENOMEM.
+ *   stream   cudaStream_t to run on, or NULL for a stream the context owns.
+ */
+typedef struct {
+    int p, n_l, n_m;
+    const double *ant_xyz;
+    const double *l, *m;
+    double lambda;
+    int cost, bound, bias_c, inflate;
+    double alpha, kappa, eps_floor;
+    double lsqr_atol, lsqr_btol;
+    int lsqr_maxit, max_outer;
+    int precision;
+    int support_cap;
+    void *stream;
+} img_params;
+
+/* Per-solve report. */
+typedef struct {
+    int status;          /* img_status of the solve                          */
+    int outer;           /* passes of the Table I loop                       */
+    int lsqr_iters;      /* LSQR iterations summed over all subproblems      */
+    int n_free;          /* |F| at return                                    */
+    int n_upper;         /* |U| at return                                    */
+    int converged;       /* 1 when no multiplier is below its threshold      */
+    double lambda_min;   /* smallest multiplier at the last gradient         */
+    double op_flops;     /* algorithmic operator flops (Psi: 4p^2|S|,
+                            Psi^H: 8p^2|S|) spent in this solve              */
+} img_solve_info;
+
+/* Fill *prm with defaults: PWLS, MVDR bound, C = 1, no inflation, kappa 6,
+ * eps_floor 1e-6, LSQR atol = btol = 1e-6, maxit 0, max_outer 0, FP32. */
+void img_params_default(img_params *prm);
+
+/* Validate *prm, copy it, and allocate all device state for one job on the
+ * current CUDA device.  *out is NULL on failure.  Errors: IMG_EINVAL (bad
+ * sizes, z != 0, lambda <= 0, unknown enum), IMG_ENOMEM, IMG_ECUDA. */
+img_status img_create(const img_params *prm, img_ctx **out);
+
+/* Load the sample covariance R_hat = (1/N) sum_n y[n] y[n]^H (Sec. II).
+ *   R      p x p Hermitian, column-major, dtype IMG_C64 or IMG_C128
+ *   N      number of samples; must exceed p (R_hat singular otherwise and
+ *          C undefined) -> else IMG_EINVAL
+ * Host input is checked for finite, Hermitian (relative 1e-6) values with a
+ * positive real diagonal.  Previous bounds and images are invalidated.  The
+ * Cholesky factor is computed on the device at the next call that needs it;
+ * a non-PD R_hat then makes that call return IMG_ENOTPD. */
+img_status img_set_covariance(img_ctx *ctx, const void *R, int dtype,
+                              long long N, int on_device);
+
+/* Matched-filter dirty image sigma_MF,i = a_i^H R_hat a_i (eq. mfdimg, K=1)
+ * written to out[0..Q).  Errors: IMG_EINVAL before img_set_covariance,
+ * IMG_ENOTPD. */
+img_status img_dirty(img_ctx *ctx, double *out, int on_device);
+
+/* Upper bound gamma used by the solver (Sec. III-D): for IMG_BOUND_MVDR
+ * C / (a_i^H R_hat^-1 a_i) (eq. wmvdr and the unbiased form with C),
+ * for IMG_BOUND_MF the dirty image, each inflated as configured. */
+img_status img_mvdr_bound(img_ctx *ctx, double *out, int on_device);
+
+/* Bounded least-squares image (Table I with LSQR subproblems) into
+ * sigma[0..Q).  info may be NULL.  Returns IMG_ENOTCONV when max_outer is
+ * reached (sigma holds the last feasible image), IMG_ENOMEM when
+ * support_cap is exceeded. */
+img_status img_solve(img_ctx *ctx, double *sigma, img_solve_info *info,
+                     int on_device);
+
+/* Pixel sets of the last solve (IMG_SET_L / _U / _F per pixel) into
+ * sets[0..Q), host memory. */
+img_status img_get_sets(img_ctx *ctx, unsigned char *sets);
+
+/* Gradient g (eq. gls or eq. gmvdr, in the solver variable) at the last
+ * solve's final image into grad[0..Q), host memory. */
+img_status img_get_gradient(img_ctx *ctx, double *grad);
+
+/* Forward operator Psi x = vect(A diag(x) A^H) (notation section; Sec. V-B):
+ * x[0..Q) real (double) -> Kout p x p complex128 column-major. */
+img_status img_psi(img_ctx *ctx, const double *x, double *Kout, int on_device);
+
+/* Adjoint operator (Psi^H vect(U))_i = Re(a_i^H U a_i) (Sec. V-B):
+ * U p x p Hermitian complex128 column-major -> out[0..Q) double. */
+img_status img_psi_adj(img_ctx *ctx, const double *U, double *out, int on_device);
+
+/* Batch of independent jobs in single launches (the paper has no batching;
+ * jobs are independent, Sec. V-B).  Every context must hold a covariance and
+ * use the same device.  sigma[j] receives job j's image (host or device per
+ * on_device), infos[j] its report (may be NULL).  Uses ctxs[0]'s stream.
+ * Returns the first non-OK job status, or IMG_OK. */
+img_status img_solve_batch(img_ctx *const *ctxs, int n, double *const *sigma,
+                           img_solve_info *infos, int on_device);
+
+/* Release all device memory of ctx.  NULL is allowed. */
+void img_destroy(img_ctx *ctx);
+
+/* Static string for a status code. */
+const char *img_status_str(img_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IMG_GB300_H */

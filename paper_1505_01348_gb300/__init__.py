@@ -1,0 +1,15 @@
+"""GB300 bounded least-squares radio imager (active set + LSQR on Khatri-Rao
+operators), a CUDA library behind the C ABI of include/img.h.
+
+Importing the package does not load the library; the first call does, and it
+raises when the library has not been built.
+"""
+from ._lib import (BOUND_MF, BOUND_MVDR, C64, C128, COST_LS, COST_PWLS, IMG_ENOTCONV,
+                   IMG_ENOTPD, IMG_OK, INFLATE_NONE, INFLATE_RATIO, INFLATE_STD, PREC_BF16X3,
+                   PREC_FP32, PREC_TF32X3, SET_F, SET_L, SET_U, ImgError, Imager, SolveInfo,
+                   load, solve_batch)
+
+__all__ = ["Imager", "solve_batch", "load", "ImgError", "SolveInfo", "COST_LS", "COST_PWLS",
+           "BOUND_MF", "BOUND_MVDR", "INFLATE_NONE", "INFLATE_RATIO", "INFLATE_STD", "C64",
+           "C128", "PREC_FP32", "PREC_TF32X3", "PREC_BF16X3", "SET_L", "SET_U", "SET_F",
+           "IMG_OK", "IMG_ENOTCONV", "IMG_ENOTPD"]

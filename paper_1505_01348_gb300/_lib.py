@@ -1,0 +1,248 @@
+"""ctypes binding of the C ABI in include/img.h (argument marshalling only).
+
+Every computation happens in the CUDA library; this module converts numpy
+arrays or torch CUDA tensors into pointers and status codes into exceptions.
+It raises when the library is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+IMG_OK, IMG_EINVAL, IMG_ENOMEM, IMG_ENOTPD, IMG_ENOTCONV, IMG_ETIMEOUT, IMG_ECUDA = range(7)
+COST_LS, COST_PWLS = 0, 1
+BOUND_MF, BOUND_MVDR = 0, 1
+INFLATE_NONE, INFLATE_RATIO, INFLATE_STD = 0, 1, 2
+C64, C128 = 0, 1
+PREC_FP32, PREC_TF32X3, PREC_BF16X3 = 0, 1, 2
+SET_L, SET_U, SET_F = 0, 1, 2
+
+EXPORTS = ("img_params_default", "img_create", "img_set_covariance", "img_dirty",
+           "img_mvdr_bound", "img_solve", "img_get_sets", "img_get_gradient", "img_psi",
+           "img_psi_adj", "img_solve_batch", "img_destroy", "img_status_str")
+
+
+class ImgParams(C.Structure):
+    _fields_ = [("p", C.c_int), ("n_l", C.c_int), ("n_m", C.c_int),
+                ("ant_xyz", C.POINTER(C.c_double)), ("l", C.POINTER(C.c_double)),
+                ("m", C.POINTER(C.c_double)), ("lambda_", C.c_double),
+                ("cost", C.c_int), ("bound", C.c_int), ("bias_c", C.c_int), ("inflate", C.c_int),
+                ("alpha", C.c_double), ("kappa", C.c_double), ("eps_floor", C.c_double),
+                ("lsqr_atol", C.c_double), ("lsqr_btol", C.c_double),
+                ("lsqr_maxit", C.c_int), ("max_outer", C.c_int),
+                ("precision", C.c_int), ("support_cap", C.c_int), ("stream", C.c_void_p)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("status", C.c_int), ("outer", C.c_int), ("lsqr_iters", C.c_int),
+                ("n_free", C.c_int), ("n_upper", C.c_int), ("converged", C.c_int),
+                ("lambda_min", C.c_double), ("op_flops", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ImgError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {status_str(code)} ({code})")
+
+
+_LIB = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False) -> C.CDLL:
+    """Load the CUDA library; raise when it is absent (no CPU fallback)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise RuntimeError(f"CUDA library {_build.LIB} is not built; run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        _build.build()
+    lib = C.CDLL(_build.LIB)
+    vp, i, ll, dp = C.c_void_p, C.c_int, C.c_longlong, C.c_void_p
+    lib.img_params_default.argtypes = [C.POINTER(ImgParams)]
+    lib.img_params_default.restype = None
+    lib.img_create.argtypes = [C.POINTER(ImgParams), C.POINTER(vp)]
+    lib.img_create.restype = i
+    lib.img_set_covariance.argtypes = [vp, dp, i, ll, i]
+    lib.img_set_covariance.restype = i
+    for name in ("img_dirty", "img_mvdr_bound"):
+        getattr(lib, name).argtypes = [vp, dp, i]
+        getattr(lib, name).restype = i
+    lib.img_solve.argtypes = [vp, dp, C.POINTER(SolveInfo), i]
+    lib.img_solve.restype = i
+    lib.img_get_sets.argtypes = [vp, dp]
+    lib.img_get_sets.restype = i
+    lib.img_get_gradient.argtypes = [vp, dp]
+    lib.img_get_gradient.restype = i
+    lib.img_psi.argtypes = [vp, dp, dp, i]
+    lib.img_psi.restype = i
+    lib.img_psi_adj.argtypes = [vp, dp, dp, i]
+    lib.img_psi_adj.restype = i
+    lib.img_solve_batch.argtypes = [C.POINTER(vp), i, C.POINTER(dp), C.POINTER(SolveInfo), i]
+    lib.img_solve_batch.restype = i
+    lib.img_destroy.argtypes = [vp]
+    lib.img_destroy.restype = None
+    lib.img_status_str.argtypes = [i]
+    lib.img_status_str.restype = C.c_char_p
+    _LIB = lib
+    return lib
+
+
+def status_str(code: int) -> str:
+    try:
+        return load().img_status_str(code).decode()
+    except Exception:  # library missing: still format the code
+        return f"status {code}"
+
+
+def _check(code: int, where: str, allow=()):
+    if code != IMG_OK and code not in allow:
+        raise ImgError(code, where)
+    return code
+
+
+def _ptr(a) -> int:
+    """Address of a contiguous numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"] or a.flags["F_CONTIGUOUS"]
+        return a.ctypes.data
+    return int(a.data_ptr())
+
+
+def _is_device(a) -> bool:
+    return not isinstance(a, np.ndarray) and getattr(a, "is_cuda", False)
+
+
+def default_params() -> ImgParams:
+    prm = ImgParams()
+    load().img_params_default(C.byref(prm))
+    return prm
+
+
+class Imager:
+    """One imaging job on the GPU (wraps an img_ctx)."""
+
+    def __init__(self, ant_xyz, l, m, lam: float = 1.0, **kw):
+        self._lib = load()
+        self.ant = np.ascontiguousarray(ant_xyz, dtype=np.float64)
+        self.l = np.ascontiguousarray(l, dtype=np.float64)
+        self.m = np.ascontiguousarray(m, dtype=np.float64)
+        prm = default_params()
+        prm.p = self.ant.shape[0]
+        prm.n_l = self.l.shape[0]
+        prm.n_m = self.m.shape[0]
+        prm.ant_xyz = self.ant.ctypes.data_as(C.POINTER(C.c_double))
+        prm.l = self.l.ctypes.data_as(C.POINTER(C.c_double))
+        prm.m = self.m.ctypes.data_as(C.POINTER(C.c_double))
+        prm.lambda_ = float(lam)
+        for k, v in kw.items():
+            if k == "stream":
+                prm.stream = C.c_void_p(int(v))
+            else:
+                setattr(prm, k, v)
+        self.prm = prm
+        self.p, self.Q = prm.p, prm.n_l * prm.n_m
+        h = C.c_void_p()
+        _check(self._lib.img_create(C.byref(prm), C.byref(h)), "img_create")
+        self.h = h
+
+    @classmethod
+    def from_job(cls, job, **kw):
+        obj = cls(job.ant_xyz, job.l, job.m, job.lam, **kw)
+        obj.set_covariance(job.R, job.N)
+        return obj
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self._lib.img_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_covariance(self, R, N: int):
+        if _is_device(R):
+            import torch
+            dt = C128 if R.dtype == torch.complex128 else C64
+            code = self._lib.img_set_covariance(self.h, _ptr(R), dt, int(N), 1)
+        else:
+            R = np.asfortranarray(R)
+            dt = C128 if R.dtype == np.complex128 else C64
+            if R.dtype not in (np.complex64, np.complex128):
+                R = np.asfortranarray(R, dtype=np.complex128)
+                dt = C128
+            code = self._lib.img_set_covariance(self.h, R.ctypes.data, dt, int(N), 0)
+        _check(code, "img_set_covariance")
+
+    def _qvec(self, fn, out, name, allow=()):
+        if out is None:
+            out = np.empty(self.Q, dtype=np.float64)
+        code = fn(self.h, _ptr(out), 1 if _is_device(out) else 0)
+        _check(code, name, allow)
+        return out
+
+    def dirty(self, out=None):
+        return self._qvec(self._lib.img_dirty, out, "img_dirty")
+
+    def mvdr_bound(self, out=None):
+        return self._qvec(self._lib.img_mvdr_bound, out, "img_mvdr_bound")
+
+    def solve(self, out=None, allow=(IMG_ENOTCONV,)):
+        if out is None:
+            out = np.empty(self.Q, dtype=np.float64)
+        info = SolveInfo()
+        code = self._lib.img_solve(self.h, _ptr(out), C.byref(info), 1 if _is_device(out) else 0)
+        _check(code, "img_solve", allow)
+        return out, info
+
+    def sets(self):
+        out = np.empty(self.Q, dtype=np.uint8)
+        _check(self._lib.img_get_sets(self.h, out.ctypes.data), "img_get_sets")
+        return out
+
+    def gradient(self):
+        out = np.empty(self.Q, dtype=np.float64)
+        _check(self._lib.img_get_gradient(self.h, out.ctypes.data), "img_get_gradient")
+        return out
+
+    def psi(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        K = np.empty((self.p, self.p), dtype=np.complex128, order="F")
+        _check(self._lib.img_psi(self.h, x.ctypes.data, K.ctypes.data, 0), "img_psi")
+        return K
+
+    def psi_adj(self, U):
+        U = np.asfortranarray(U, dtype=np.complex128)
+        out = np.empty(self.Q, dtype=np.float64)
+        _check(self._lib.img_psi_adj(self.h, U.ctypes.data, out.ctypes.data, 0), "img_psi_adj")
+        return out
+
+
+def solve_batch(imagers, outs=None, allow=(IMG_ENOTCONV,)):
+    """Solve several jobs in one launch; returns (images, infos)."""
+    lib = load()
+    n = len(imagers)
+    if outs is None:
+        outs = [np.empty(im.Q, dtype=np.float64) for im in imagers]
+    dev = 1 if _is_device(outs[0]) else 0
+    hs = (C.c_void_p * n)(*[im.h.value for im in imagers])
+    ps = (C.c_void_p * n)(*[_ptr(o) for o in outs])
+    infos = (SolveInfo * n)()
+    code = lib.img_solve_batch(hs, n, ps, infos, dev)
+    _check(code, "img_solve_batch", allow)
+    return outs, list(infos)

@@ -1,0 +1,504 @@
+// Host side of the C ABI declared in include/img.h: validation, device
+// memory layout of a job, and the launch sequence of every call.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/img.h"
+#include "img_internal.cuh"
+
+using img::DevInfo;
+using img::JobDev;
+
+struct img_ctx {
+    img_params prm;
+    std::vector<double> ant, l, m;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void *dmem = nullptr;
+    size_t dbytes = 0;
+    JobDev hj{};                 // host mirror (device pointers)
+    JobDev *dj = nullptr;        // device copy of hj
+    JobDev **djp = nullptr;      // device array {dj} for single-job launches
+    bool has_cov = false;
+    bool prepared = false;
+    int prep_status = IMG_OK;
+    bool solved = false;
+    // operator scratch
+    float *wx = nullptr;
+    float2 *part = nullptr;
+    int nparts = 0;
+    float2 *U32 = nullptr;
+    double2 *Z = nullptr;        // p*p complex128 staging
+    double *outd = nullptr;      // Q doubles staging
+};
+
+namespace {
+
+constexpr int kMaxP = 384;
+
+img_status cuda_status(cudaError_t e) { return e == cudaSuccess ? IMG_OK : IMG_ECUDA; }
+
+#define CK(x)                                        \
+    do {                                             \
+        cudaError_t _e = (x);                        \
+        if (_e != cudaSuccess) return IMG_ECUDA;     \
+    } while (0)
+
+struct Carver {
+    char *base;
+    size_t off = 0;
+    template <class T>
+    T *take(size_t n) {
+        off = (off + 255) & ~size_t(255);
+        T *p = reinterpret_cast<T *>(base ? base + off : nullptr);
+        off += n * sizeof(T);
+        return p;
+    }
+};
+
+// Lay out every device array of one job; with base == nullptr only sizes.
+size_t carve(img_ctx *c, char *base) {
+    const int p = c->prm.p, nl = c->prm.n_l, nm = c->prm.n_m;
+    const int Q = nl * nm;
+    const int cap = c->hj.cap;
+    Carver cv{base};
+    JobDev &J = c->hj;
+    J.ant = cv.take<double>(3 * (size_t)p);
+    J.lg = cv.take<double>(nl);
+    J.mg = cv.take<double>(nm);
+    const size_t pp = (size_t)p * p;
+    J.R64 = cv.take<double2>(pp);
+    J.L64 = cv.take<double2>(pp);
+    J.Li64 = cv.take<double2>(pp);
+    J.R32 = cv.take<float2>(pp);
+    J.Ri32 = cv.take<float2>(pp);
+    J.Li32 = cv.take<float2>(pp);
+    J.El = cv.take<float2>((size_t)nl * p);
+    J.Em = cv.take<float2>((size_t)nm * p);
+    J.dirty = cv.take<float>(Q);
+    J.h = cv.take<float>(Q);
+    J.scale = cv.take<float>(Q);
+    J.eps = cv.take<float>(Q);
+    J.grad = cv.take<float>(Q);
+    J.upper = cv.take<double>(Q);
+    J.gamma = cv.take<double>(Q);
+    J.mvb = cv.take<double>(Q);
+    J.x = cv.take<double>(Q);
+    J.sigma = cv.take<double>(Q);
+    J.set = cv.take<unsigned char>(Q);
+    J.slot = cv.take<int>(Q);
+    J.supp = cv.take<int>(cap);
+    J.cvec = cv.take<float2>((size_t)cap * p);
+    J.fpos = cv.take<int>(cap);
+    J.v = cv.take<float>(cap);
+    J.w = cv.take<float>(cap);
+    J.xs = cv.take<float>(2 * (size_t)cap);
+    J.W0 = cv.take<float2>(pp);
+    J.W1 = cv.take<float2>(pp);
+    J.W2 = cv.take<float2>(pp);
+    J.info = cv.take<DevInfo>(1);
+    J.flags = cv.take<int>(4);
+    c->dj = cv.take<JobDev>(1);
+    c->djp = cv.take<JobDev *>(1);
+    c->wx = cv.take<float>(Q);
+    c->part = cv.take<float2>((size_t)c->nparts * pp);
+    c->U32 = cv.take<float2>(pp);
+    c->Z = cv.take<double2>(pp);
+    c->outd = cv.take<double>(Q);
+    return cv.off + 256;
+}
+
+bool finite_all(const double *v, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+img_status sync(img_ctx *c) { return cuda_status(cudaStreamSynchronize(c->stream)); }
+
+// Factor, dirty image, bounds (once per covariance).
+img_status prepare(img_ctx *c) {
+    if (!c->has_cov) return IMG_EINVAL;
+    if (c->prepared) return (img_status)c->prep_status;
+    CK(img::launch_factor(c->djp, 1, c->stream));
+    const int ntiles = (c->hj.Q + img::kTile - 1) / img::kTile;
+    CK(img::launch_bounds(c->djp, 1, ntiles, c->prm.p, c->stream));
+    CK(img::launch_finalize(c->djp, 1, c->stream));
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, c->hj.flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->prepared = true;
+    c->prep_status = flag == 0 ? IMG_OK : IMG_ENOTPD;
+    return (img_status)c->prep_status;
+}
+
+img_status copy_out_double(img_ctx *c, const double *src, double *dst, size_t n, int on_device) {
+    CK(cudaMemcpyAsync(dst, src, n * sizeof(double),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    return sync(c);
+}
+
+img_status copy_out_float(img_ctx *c, const float *src, double *dst, size_t n, int on_device) {
+    if (on_device) {
+        CK(img::launch_to_double(src, dst, (int)n, c->stream));
+        return sync(c);
+    }
+    CK(img::launch_to_double(src, c->outd, (int)n, c->stream));
+    return copy_out_double(c, c->outd, dst, n, 0);
+}
+
+// Batch workspace shared by img_solve_batch calls (grown on demand).
+struct BatchWs {
+    std::mutex mu;
+    int cap = 0;
+    int device = -1;
+    JobDev **jobs = nullptr;
+    DevInfo *infos = nullptr;
+    double **sig = nullptr;
+};
+BatchWs g_ws;
+
+img_status ws_reserve(int n, int device) {
+    if (g_ws.cap >= n && g_ws.device == device) return IMG_OK;
+    if (g_ws.jobs) {
+        cudaFree(g_ws.jobs);
+        g_ws.jobs = nullptr;
+    }
+    int cap = 64;
+    while (cap < n) cap *= 2;
+    size_t bytes = cap * (sizeof(JobDev *) + sizeof(DevInfo) + sizeof(double *)) + 512;
+    char *b = nullptr;
+    CK(cudaMalloc(&b, bytes));
+    g_ws.jobs = reinterpret_cast<JobDev **>(b);
+    g_ws.sig = reinterpret_cast<double **>(b + cap * sizeof(JobDev *));
+    g_ws.infos = reinterpret_cast<DevInfo *>(
+        b + ((cap * (sizeof(JobDev *) + sizeof(double *)) + 255) & ~size_t(255)));
+    g_ws.cap = cap;
+    g_ws.device = device;
+    return IMG_OK;
+}
+
+void fill_info(img_solve_info *o, const DevInfo &d) {
+    o->status = d.status;
+    o->outer = d.outer;
+    o->lsqr_iters = d.lsqr_iters;
+    o->n_free = d.n_free;
+    o->n_upper = d.n_upper;
+    o->converged = d.converged;
+    o->lambda_min = d.lambda_min;
+    o->op_flops = d.op_flops;
+}
+
+}  // namespace
+
+extern "C" {
+
+void img_params_default(img_params *prm) {
+    if (!prm) return;
+    std::memset(prm, 0, sizeof(*prm));
+    prm->lambda = 1.0;
+    prm->cost = IMG_COST_PWLS;
+    prm->bound = IMG_BOUND_MVDR;
+    prm->bias_c = 0;
+    prm->inflate = IMG_INFLATE_NONE;
+    prm->alpha = 6.0;
+    prm->kappa = 6.0;
+    prm->eps_floor = 1e-6;
+    prm->lsqr_atol = 1e-6;
+    prm->lsqr_btol = 1e-6;
+    prm->precision = IMG_PREC_FP32;
+}
+
+const char *img_status_str(img_status s) {
+    switch (s) {
+        case IMG_OK: return "ok";
+        case IMG_EINVAL: return "invalid argument or call order";
+        case IMG_ENOMEM: return "out of memory or capacity";
+        case IMG_ENOTPD: return "covariance not positive definite";
+        case IMG_ENOTCONV: return "active-set loop did not converge";
+        case IMG_ETIMEOUT: return "device wait timed out";
+        case IMG_ECUDA: return "CUDA error";
+    }
+    return "unknown status";
+}
+
+img_status img_create(const img_params *prm, img_ctx **out) {
+    if (!out) return IMG_EINVAL;
+    *out = nullptr;
+    if (!prm) return IMG_EINVAL;
+    const img_params &P = *prm;
+    if (P.p < 2 || P.p > kMaxP || P.n_l < 1 || P.n_m < 1) return IMG_EINVAL;
+    if ((long long)P.n_l * P.n_m > (1LL << 24)) return IMG_EINVAL;
+    if (!P.ant_xyz || !P.l || !P.m) return IMG_EINVAL;
+    if (!(P.lambda > 0.0) || !std::isfinite(P.lambda)) return IMG_EINVAL;
+    if (P.cost != IMG_COST_LS && P.cost != IMG_COST_PWLS) return IMG_EINVAL;
+    if (P.bound != IMG_BOUND_MF && P.bound != IMG_BOUND_MVDR) return IMG_EINVAL;
+    if (P.inflate < IMG_INFLATE_NONE || P.inflate > IMG_INFLATE_STD) return IMG_EINVAL;
+    if (P.precision < IMG_PREC_FP32 || P.precision > IMG_PREC_BF16X3) return IMG_EINVAL;
+    if (!(P.kappa >= 0.0) || !(P.eps_floor >= 0.0) || !(P.alpha >= 0.0)) return IMG_EINVAL;
+    if (!(P.lsqr_atol >= 0.0) || !(P.lsqr_btol >= 0.0) || P.lsqr_maxit < 0 || P.max_outer < 0)
+        return IMG_EINVAL;
+    if (P.support_cap < 0) return IMG_EINVAL;
+    if (!finite_all(P.ant_xyz, 3 * (size_t)P.p) || !finite_all(P.l, P.n_l) || !finite_all(P.m, P.n_m))
+        return IMG_EINVAL;
+    for (int k = 0; k < P.p; ++k)
+        if (P.ant_xyz[3 * k + 2] != 0.0) return IMG_EINVAL;
+
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return IMG_ECUDA;
+    img_ctx *c = new (std::nothrow) img_ctx();
+    if (!c) return IMG_ENOMEM;
+    c->prm = P;
+    c->ant.assign(P.ant_xyz, P.ant_xyz + 3 * P.p);
+    c->l.assign(P.l, P.l + P.n_l);
+    c->m.assign(P.m, P.m + P.n_m);
+    c->prm.ant_xyz = c->ant.data();
+    c->prm.l = c->l.data();
+    c->prm.m = c->m.data();
+    cudaGetDevice(&c->device);
+    if (P.stream) {
+        c->stream = (cudaStream_t)P.stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return IMG_ECUDA;
+        }
+        c->own_stream = true;
+    }
+    const int Q = P.n_l * P.n_m;
+    JobDev &J = c->hj;
+    J.p = P.p;
+    J.n_l = P.n_l;
+    J.n_m = P.n_m;
+    J.Q = Q;
+    J.cost = P.cost;
+    J.bound = P.bound;
+    J.bias_c = P.bias_c ? 1 : 0;
+    J.inflate = P.inflate;
+    J.lsqr_maxit = P.lsqr_maxit;
+    J.max_outer = P.max_outer;
+    J.cap = P.support_cap > 0 ? std::min(P.support_cap, Q) : std::min(Q, 16384);
+    J.precision = P.precision;
+    J.alpha = P.alpha;
+    J.kappa = P.kappa;
+    J.eps_floor = P.eps_floor;
+    J.lam = P.lambda;
+    J.lsqr_atol = P.lsqr_atol;
+    J.lsqr_btol = P.lsqr_btol;
+    J.N = 0;
+    {
+        int sms = 1;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+        const size_t pp8 = (size_t)P.p * P.p * sizeof(float2);
+        int np = 2 * std::max(1, sms);
+        const int lim = (int)std::max<size_t>(1, (4u << 20) / pp8);
+        c->nparts = std::max(1, std::min(np, lim));
+    }
+    c->dbytes = carve(c, nullptr);
+    if (cudaMalloc(&c->dmem, c->dbytes) != cudaSuccess) {
+        if (c->own_stream) cudaStreamDestroy(c->stream);
+        delete c;
+        return IMG_ENOMEM;
+    }
+    carve(c, reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(c->dmem) + 255) & ~uintptr_t(255)));
+    img_status st = IMG_OK;
+    int init_flags[4] = {-1, 0, 0, 0};
+    if (cudaMemcpyAsync((void *)J.ant, c->ant.data(), 3 * P.p * sizeof(double), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync((void *)J.lg, c->l.data(), P.n_l * sizeof(double), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync((void *)J.mg, c->m.data(), P.n_m * sizeof(double), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(J.flags, init_flags, sizeof(init_flags), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(c->dj, &J, sizeof(JobDev), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(c->djp, &c->dj, sizeof(JobDev *), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        img::launch_tables(c->djp, 1, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        st = IMG_ECUDA;
+    if (st != IMG_OK) {
+        img_destroy(c);
+        return st;
+    }
+    *out = c;
+    return IMG_OK;
+}
+
+img_status img_set_covariance(img_ctx *c, const void *R, int dtype, long long N, int on_device) {
+    if (!c || !R) return IMG_EINVAL;
+    if (dtype != IMG_C64 && dtype != IMG_C128) return IMG_EINVAL;
+    const int p = c->prm.p;
+    if (N <= p) return IMG_EINVAL;
+    const size_t pp = (size_t)p * p;
+    c->has_cov = false;
+    c->prepared = false;
+    c->solved = false;
+    if (!on_device) {
+        std::vector<double> z(2 * pp);
+        if (dtype == IMG_C128) {
+            std::memcpy(z.data(), R, 2 * pp * sizeof(double));
+        } else {
+            const float *f = static_cast<const float *>(R);
+            for (size_t e = 0; e < 2 * pp; ++e) z[e] = f[e];
+        }
+        if (!finite_all(z.data(), z.size())) return IMG_EINVAL;
+        double mx = 0.0;
+        for (double v : z) mx = std::max(mx, std::fabs(v));
+        for (int k = 0; k < p; ++k) {
+            if (!(z[2 * ((size_t)k * p + k)] > 0.0)) return IMG_EINVAL;
+            for (int l = 0; l < p; ++l) {
+                const double *a = &z[2 * ((size_t)l * p + k)];
+                const double *b = &z[2 * ((size_t)k * p + l)];
+                if (std::fabs(a[0] - b[0]) > 1e-6 * mx || std::fabs(a[1] + b[1]) > 1e-6 * mx)
+                    return IMG_EINVAL;
+            }
+        }
+        CK(cudaMemcpyAsync(c->hj.R64, z.data(), 2 * pp * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    } else {
+        if (dtype == IMG_C128) {
+            CK(cudaMemcpyAsync(c->hj.R64, R, pp * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+        } else {
+            CK(img::launch_c2z(static_cast<const float2 *>(R), c->hj.R64, (int)pp, c->stream));
+        }
+    }
+    c->hj.N = N;
+    int init_flags[2] = {-1, 0};
+    CK(cudaMemcpyAsync(&c->dj->N, &c->hj.N, sizeof(long long), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->hj.flags, init_flags, sizeof(init_flags), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->has_cov = true;
+    return IMG_OK;
+}
+
+img_status img_dirty(img_ctx *c, double *out, int on_device) {
+    if (!c || !out) return IMG_EINVAL;
+    img_status st = prepare(c);
+    if (st != IMG_OK) return st;
+    return copy_out_float(c, c->hj.dirty, out, c->hj.Q, on_device);
+}
+
+img_status img_mvdr_bound(img_ctx *c, double *out, int on_device) {
+    if (!c || !out) return IMG_EINVAL;
+    img_status st = prepare(c);
+    if (st != IMG_OK) return st;
+    return copy_out_double(c, c->hj.mvb, out, c->hj.Q, on_device);
+}
+
+img_status img_solve(img_ctx *c, double *sigma, img_solve_info *info, int on_device) {
+    if (!c || !sigma) return IMG_EINVAL;
+    img_status st = prepare(c);
+    if (st != IMG_OK) return st;
+    CK(img::launch_solve(c->djp, 1, c->prm.p, nullptr, nullptr, c->stream));
+    DevInfo d{};
+    CK(cudaMemcpyAsync(&d, c->hj.info, sizeof(DevInfo), cudaMemcpyDeviceToHost, c->stream));
+    st = copy_out_double(c, c->hj.sigma, sigma, c->hj.Q, on_device);
+    if (st != IMG_OK) return st;
+    if (info) fill_info(info, d);
+    c->solved = true;
+    return (img_status)d.status;
+}
+
+img_status img_get_sets(img_ctx *c, unsigned char *sets) {
+    if (!c || !sets || !c->solved) return IMG_EINVAL;
+    CK(cudaMemcpyAsync(sets, c->hj.set, c->hj.Q, cudaMemcpyDeviceToHost, c->stream));
+    return sync(c);
+}
+
+img_status img_get_gradient(img_ctx *c, double *grad) {
+    if (!c || !grad || !c->solved) return IMG_EINVAL;
+    return copy_out_float(c, c->hj.grad, grad, c->hj.Q, 0);
+}
+
+img_status img_psi(img_ctx *c, const double *x, double *Kout, int on_device) {
+    if (!c || !x || !Kout) return IMG_EINVAL;
+    const int Q = c->hj.Q, p = c->prm.p;
+    if (on_device) {
+        CK(img::launch_d2f(x, c->wx, Q, c->stream));
+    } else {
+        std::vector<float> f(Q);
+        for (int i = 0; i < Q; ++i) f[i] = (float)x[i];
+        CK(cudaMemcpyAsync(c->wx, f.data(), Q * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    CK(img::launch_psi(c->dj, c->wx, c->part, c->nparts, Q, p, c->Z, c->stream));
+    CK(cudaMemcpyAsync(Kout, c->Z, (size_t)p * p * sizeof(double2),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    return sync(c);
+}
+
+img_status img_psi_adj(img_ctx *c, const double *U, double *out, int on_device) {
+    if (!c || !U || !out) return IMG_EINVAL;
+    const int Q = c->hj.Q, p = c->prm.p;
+    CK(cudaMemcpyAsync(c->Z, U, (size_t)p * p * sizeof(double2),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    CK(img::launch_z2c(c->Z, c->U32, p * p, c->stream));
+    CK(img::launch_psi_adj(c->dj, c->U32, on_device ? out : c->outd, Q, p, c->stream));
+    if (on_device) return sync(c);
+    return copy_out_double(c, c->outd, out, Q, 0);
+}
+
+img_status img_solve_batch(img_ctx *const *ctxs, int n, double *const *sigma, img_solve_info *infos,
+                           int on_device) {
+    if (!ctxs || n <= 0 || !sigma) return IMG_EINVAL;
+    for (int j = 0; j < n; ++j) {
+        if (!ctxs[j] || !sigma[j] || !ctxs[j]->has_cov) return IMG_EINVAL;
+        if (ctxs[j]->device != ctxs[0]->device) return IMG_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(g_ws.mu);
+    img_status st = ws_reserve(n, ctxs[0]->device);
+    if (st != IMG_OK) return st;
+    cudaStream_t s = ctxs[0]->stream;
+    // make every context's earlier work visible on the batch stream
+    for (int j = 0; j < n; ++j)
+        if (ctxs[j]->stream != s) CK(cudaStreamSynchronize(ctxs[j]->stream));
+    std::vector<JobDev *> ptrs(n);
+    std::vector<JobDev *> prep;
+    int max_p = 0, max_tiles = 1;
+    for (int j = 0; j < n; ++j) {
+        ptrs[j] = ctxs[j]->dj;
+        max_p = std::max(max_p, ctxs[j]->prm.p);
+        if (!ctxs[j]->prepared) {
+            prep.push_back(ctxs[j]->dj);
+            max_tiles = std::max(max_tiles, (ctxs[j]->hj.Q + img::kTile - 1) / img::kTile);
+        }
+    }
+    if (!prep.empty()) {
+        int np = (int)prep.size();
+        CK(cudaMemcpyAsync(g_ws.jobs, prep.data(), np * sizeof(JobDev *), cudaMemcpyHostToDevice, s));
+        CK(img::launch_factor(g_ws.jobs, np, s));
+        CK(img::launch_bounds(g_ws.jobs, np, max_tiles, max_p, s));
+        CK(img::launch_finalize(g_ws.jobs, np, s));
+    }
+    CK(cudaMemcpyAsync(g_ws.jobs, ptrs.data(), n * sizeof(JobDev *), cudaMemcpyHostToDevice, s));
+    if (on_device)
+        CK(cudaMemcpyAsync(g_ws.sig, sigma, n * sizeof(double *), cudaMemcpyHostToDevice, s));
+    CK(img::launch_solve(g_ws.jobs, n, max_p, g_ws.infos, on_device ? g_ws.sig : nullptr, s));
+    std::vector<DevInfo> d(n);
+    CK(cudaMemcpyAsync(d.data(), g_ws.infos, n * sizeof(DevInfo), cudaMemcpyDeviceToHost, s));
+    if (!on_device)
+        for (int j = 0; j < n; ++j)
+            CK(cudaMemcpyAsync(sigma[j], ctxs[j]->hj.sigma, ctxs[j]->hj.Q * sizeof(double),
+                               cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    img_status first = IMG_OK;
+    for (int j = 0; j < n; ++j) {
+        ctxs[j]->prepared = true;
+        ctxs[j]->prep_status = d[j].status == IMG_ENOTPD ? IMG_ENOTPD : IMG_OK;
+        ctxs[j]->solved = true;
+        if (infos) fill_info(&infos[j], d[j]);
+        if (first == IMG_OK && d[j].status != IMG_OK) first = (img_status)d[j].status;
+    }
+    return first;
+}
+
+void img_destroy(img_ctx *c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->dmem) cudaFree(c->dmem);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+}  // extern "C"

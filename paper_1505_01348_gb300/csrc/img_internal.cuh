@@ -1,0 +1,91 @@
+// Internal device-side job layout shared by the kernels and the host API.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace img {
+
+constexpr int kThreads = 256;      // threads per CTA in every kernel
+constexpr int kTile = 64;          // pixels per operator chunk / matrix tile edge
+
+// Per-job report written by the solver (mirrors img_solve_info).
+struct DevInfo {
+    int status;
+    int outer;
+    int lsqr_iters;
+    int n_free;
+    int n_upper;
+    int converged;
+    double lambda_min;
+    double op_flops;
+};
+
+// Everything one imaging job keeps on the device.  All pointers are device
+// memory carved from one allocation owned by the host context.
+struct JobDev {
+    // sizes and parameters
+    int p, n_l, n_m, Q;
+    int cost, bound, bias_c, inflate;
+    int lsqr_maxit, max_outer, cap, precision;
+    double alpha, kappa, eps_floor, lam, lsqr_atol, lsqr_btol;
+    long long N;
+    // geometry (copied from the host)
+    const double *ant;     // p*3 row-major
+    const double *lg;      // n_l
+    const double *mg;      // n_m
+    // covariance and factors (column-major p x p)
+    double2 *R64;          // R_hat
+    double2 *L64;          // Cholesky factor, lower
+    double2 *Li64;         // L^-1, lower
+    float2 *R32;           // R_hat
+    float2 *Ri32;          // R_hat^-1
+    float2 *Li32;          // L^-1
+    // separable steering tables, pixel-major: El[il*p + k], Em[im*p + k]
+    float2 *El;
+    float2 *Em;
+    // per-pixel arrays (Q)
+    float *dirty;          // MF dirty image
+    float *h;              // a^H R^-1 a
+    float *scale;          // s_i: sigma_i = s_i x_i (1/D_i for PWLS, 1 for LS)
+    float *eps;            // detection threshold in gradient units
+    float *grad;           // last gradient (solver variable)
+    double *upper;         // bound in the solver variable
+    double *gamma;         // bound in sigma units
+    double *mvb;           // MVDR bound C/h (inflated as configured)
+    double *x;             // solver variable
+    double *sigma;         // output image
+    unsigned char *set;    // IMG_SET_*
+    int *slot;             // support slot of a pixel or -1
+    // support S = F u U: pixel ids and cached (whitened) steering vectors
+    int *supp;             // cap
+    float2 *cvec;          // cap * p, c_i = T a_i (T = L^-1 for PWLS, I for LS)
+    int *fpos;             // cap, positions in supp of the free pixels
+    float *v, *w, *xs;     // cap, LSQR vectors indexed by F position
+    float2 *W0, *W1, *W2;  // p*p scratch matrices
+    // status and report
+    DevInfo *info;
+    int *flags;            // [0]: factor status, [1]: bounds valid
+};
+
+// Kernel launchers (defined in the .cu files, called by the host API).
+// `jobs` is a device array of n job pointers.
+cudaError_t launch_tables(JobDev *const *jobs, int n, cudaStream_t st);
+cudaError_t launch_factor(JobDev *const *jobs, int n, cudaStream_t st);
+cudaError_t launch_bounds(JobDev *const *jobs, int n, int max_tiles, int max_p,
+                          cudaStream_t st);
+cudaError_t launch_finalize(JobDev *const *jobs, int n, cudaStream_t st);
+cudaError_t launch_solve(JobDev *const *jobs, int n, int max_p, DevInfo *batch_info,
+                         double *const *sigma_out, cudaStream_t st);
+cudaError_t launch_psi(const JobDev *job_dev, const float *wx, float2 *part, int nparts, int Q,
+                       int p, double2 *Kout, cudaStream_t st);
+cudaError_t launch_psi_adj(const JobDev *job_dev, const float2 *U, double *out, int Q, int p,
+                           cudaStream_t st);
+cudaError_t launch_z2c(const double2 *src, float2 *dst, int n, cudaStream_t st);
+cudaError_t launch_c2z(const float2 *src, double2 *dst, int n, cudaStream_t st);
+cudaError_t launch_d2f(const double *src, float *dst, int n, cudaStream_t st);
+cudaError_t launch_to_double(const float *src, double *dst, int n, cudaStream_t st);
+
+size_t solve_smem_bytes(int p);
+size_t bounds_smem_bytes(int p);
+
+}  // namespace img

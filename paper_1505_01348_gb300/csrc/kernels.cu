@@ -1,0 +1,755 @@
+// Kernels of the bounded least-squares imager (SIMT FP32 operator path).
+//
+//   k_tables    separable steering tables (FP64 phase reduction + sincospi)
+//   k_factor    Cholesky R = L L^H, L^-1 and R^-1 in FP64 (one CTA per job)
+//   k_bounds    dirty image a^H R a and a^H R^-1 a over all pixels (many CTAs
+//               per job), the adjoint operator with U = R_hat and R_hat^-1
+//   k_finalize  MVDR bound, D, thresholds (Sec. III-D, Appendix A)
+//   k_solve     persistent active-set + LSQR driver, one CTA per job
+//               (Table I, Sec. V-A, Sec. V-B)
+#include "cta_ops.cuh"
+#include "../../include/img.h"
+
+namespace img {
+
+// ---------------------------------------------------------------- tables
+// El[il*p+k] = p^{-1/2} exp(-j 2 pi x_k l_il / lam), Em[im*p+k] = exp(-j 2 pi y_k m_im / lam).
+// The phase argument t is reduced to r = t - rint(t) in FP64 before sincospi,
+// so phases of hundreds of turns keep full accuracy.
+__global__ void k_tables(JobDev *const *jobs) {
+    const JobDev &J = *jobs[blockIdx.y];
+    const int p = J.p;
+    const int total = p * (J.n_l + J.n_m);
+    const double sc = rsqrt((double)p);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const bool isl = e < p * J.n_l;
+        const int e2 = isl ? e : e - p * J.n_l;
+        const int g = e2 / p, k = e2 - g * p;
+        const double coord = isl ? J.ant[3 * k + 0] : J.ant[3 * k + 1];
+        const double dir = isl ? J.lg[g] : J.mg[g];
+        const double t = coord * dir / J.lam;
+        const double r = t - rint(t);
+        double s, c;
+        sincospi(2.0 * r, &s, &c);
+        if (isl) J.El[e2] = make_float2((float)(c * sc), (float)(-s * sc));
+        else J.Em[e2] = make_float2((float)c, (float)(-s));
+    }
+}
+
+// ---------------------------------------------------------------- factor
+// Right-looking Cholesky in FP64, then L^-1 by forward substitution (one
+// column per thread) and R^-1 = L^-H L^-1.  Status 0 ok, IMG_ENOTPD else.
+__global__ void k_factor(JobDev *const *jobs) {
+    const JobDev &J = *jobs[blockIdx.x];
+    const int p = J.p;
+    double2 *L = J.L64;
+    __shared__ int bad;
+    if (threadIdx.x == 0) bad = 0;
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) L[e] = J.R64[e];
+    __syncthreads();
+    for (int j = 0; j < p; ++j) {
+        // every thread reads the pivot itself; bad is written only by thread 0
+        const double d = L[(size_t)j * p + j].x;
+        const bool ok = d > 0.0 && isfinite(d);
+        if (!ok) {
+            if (threadIdx.x == 0) bad = 1;
+            break;
+        }
+        const double dj = sqrt(d);
+        const double inv = 1.0 / dj;
+        __syncthreads();
+        if (threadIdx.x == 0) L[(size_t)j * p + j] = make_double2(dj, 0.0);
+        for (int i = j + 1 + threadIdx.x; i < p; i += blockDim.x) {
+            double2 v = L[(size_t)j * p + i];
+            L[(size_t)j * p + i] = make_double2(v.x * inv, v.y * inv);
+        }
+        __syncthreads();
+        // trailing update of the lower triangle: L[i,k] -= L[i,j] conj(L[k,j]), j < k <= i
+        const int m = p - j - 1;
+        for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+            const int k = j + 1 + t / m, i = j + 1 + t % m;
+            if (i < k) continue;
+            const double2 prod = zmulc(L[(size_t)j * p + i], L[(size_t)j * p + k]);
+            const double2 v = L[(size_t)k * p + i];
+            L[(size_t)k * p + i] = make_double2(v.x - prod.x, v.y - prod.y);
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    if (bad) {
+        if (threadIdx.x == 0) J.flags[0] = IMG_ENOTPD;
+        return;
+    }
+    // zero the strict upper triangle
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        const int col = e / p, row = e - col * p;
+        if (row < col) L[e] = make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    // X = L^-1, column c by one thread
+    double2 *X = J.Li64;
+    for (int c = threadIdx.x; c < p; c += blockDim.x) {
+        for (int i = 0; i < c; ++i) X[(size_t)c * p + i] = make_double2(0.0, 0.0);
+        for (int i = c; i < p; ++i) {
+            double2 s = make_double2(i == c ? 1.0 : 0.0, 0.0);
+            for (int k = c; k < i; ++k) {
+                const double2 t = zmul(L[(size_t)k * p + i], X[(size_t)c * p + k]);
+                s.x -= t.x;
+                s.y -= t.y;
+            }
+            const double lii = L[(size_t)i * p + i].x;
+            X[(size_t)c * p + i] = make_double2(s.x / lii, s.y / lii);
+        }
+    }
+    __syncthreads();
+    // R^-1[a,b] = sum_k conj(X[k,a]) X[k,b], k >= max(a,b); FP32 copies
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        const int b = e / p, a = e - b * p;
+        double2 s = make_double2(0.0, 0.0);
+        for (int k = max(a, b); k < p; ++k) {
+            const double2 t = zmulc(X[(size_t)b * p + k], X[(size_t)a * p + k]);
+            s.x += t.x;
+            s.y += t.y;
+        }
+        J.Ri32[e] = make_float2((float)s.x, (float)s.y);
+        J.Li32[e] = make_float2((float)X[e].x, (float)X[e].y);
+        J.R32[e] = make_float2((float)J.R64[e].x, (float)J.R64[e].y);
+    }
+    if (threadIdx.x == 0) J.flags[0] = 0;
+}
+
+// ---------------------------------------------------------------- bounds
+// dirty_i = Re(a_i^H R a_i) and h_i = Re(a_i^H R^-1 a_i) for all pixels
+// (eq. mfdimg and the MVDR denominator), blockIdx.y = job.
+__global__ void k_bounds(JobDev *const *jobs) {
+    const JobDev &J = *jobs[blockIdx.y];
+    if (J.flags[0] != 0) return;
+    extern __shared__ float4 smem4[];
+    float2 *A = reinterpret_cast<float2 *>(smem4);
+    float *red = reinterpret_cast<float *>(A + J.p * kTile);
+    const int ntiles = (J.Q + kTile - 1) / kTile;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int pix0 = t * kTile;
+        const int np = min(kTile, J.Q - pix0);
+        fill_steer_adj(J, pix0, np, A);
+        __syncthreads();
+        adj_chunk(J.R32, J.p, A, red);
+        if (threadIdx.x < np) J.dirty[pix0 + threadIdx.x] = red[threadIdx.x];
+        __syncthreads();
+        adj_chunk(J.Ri32, J.p, A, red);
+        if (threadIdx.x < np) J.h[pix0 + threadIdx.x] = red[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+// Bounds, preconditioner and thresholds (one CTA per job):
+//   C = N/(N-p) or 1; mvdr = C/h; D = h^2/C; std_MF = dirty/sqrt(N);
+//   std_MVDR = mvdr/sqrt(N-p-1); gamma = chosen image, optionally inflated;
+//   PWLS: x = D sigma (scale 1/D, upper D gamma); eps = kappa std with a floor.
+__global__ void k_finalize(JobDev *const *jobs) {
+    const JobDev &J = *jobs[blockIdx.x];
+    if (J.flags[0] != 0) return;
+    __shared__ double sbuf[kThreads / 32];
+    const double C = J.bias_c ? (double)J.N / (double)(J.N - J.p) : 1.0;
+    const double sqN = sqrt((double)J.N);
+    const double dof = (double)(J.N - J.p - 1);
+    const bool pwls = J.cost == IMG_COST_PWLS;
+    double mx = 0.0;
+    for (int i = threadIdx.x; i < J.Q; i += blockDim.x) {
+        const double h = J.h[i];
+        const double d = J.dirty[i];
+        const double mv = C / h;
+        const double base = J.bound == IMG_BOUND_MF ? d : mv;
+        const double sd = J.bound == IMG_BOUND_MF ? d / sqN : (dof > 0 ? mv / sqrt(dof) : INFINITY);
+        double g = base;
+        if (J.inflate == IMG_INFLATE_RATIO) g = (1.0 + J.alpha) * base;
+        else if (J.inflate == IMG_INFLATE_STD) g = base + J.alpha * sd;
+        const double D = h * h / C;
+        double mb = mv;
+        if (J.inflate == IMG_INFLATE_RATIO) mb = (1.0 + J.alpha) * mv;
+        else if (J.inflate == IMG_INFLATE_STD) mb = mv + J.alpha * (dof > 0 ? mv / sqrt(dof) : INFINITY);
+        J.mvb[i] = mb;
+        J.gamma[i] = g;
+        J.upper[i] = pwls ? D * g : g;
+        J.scale[i] = pwls ? (float)(1.0 / D) : 1.0f;
+        const double sdc = pwls ? (dof > 0 ? mv / sqrt(dof) : INFINITY) : d / sqN;
+        J.eps[i] = (float)(J.kappa * sdc);
+        mx = fmax(mx, pwls ? mv : d);
+    }
+    // max over the CTA (all values positive)
+    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) sbuf[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    mx = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) mx = fmax(mx, sbuf[w]);
+    const float fl = (float)(J.eps_floor * mx);
+    for (int i = threadIdx.x; i < J.Q; i += blockDim.x) J.eps[i] = fmaxf(J.eps[i], fl);
+    if (threadIdx.x == 0) J.flags[1] = 1;
+}
+
+// ---------------------------------------------------------------- solver
+struct SolveShared {
+    double dbuf[kThreads / 32];
+    double vbuf[kThreads / 32];
+    int ibuf[kThreads / 32];
+    int cbuf[kThreads / 32];
+    float wsm[kTile];
+    float red[kTile + 16 * kTile];
+};
+
+// c = T a_i for the support cache (T = L^-1 for PWLS, identity for LS).
+__device__ void cache_vector(const JobDev &J, int i, int slot) {
+    const int p = J.p;
+    const int im = i / J.n_l, il = i - im * J.n_l;
+    float2 *c = J.cvec + (size_t)slot * p;
+    const bool pwls = J.cost == IMG_COST_PWLS;
+    for (int k = threadIdx.x; k < p; k += blockDim.x) {
+        if (!pwls) {
+            c[k] = steer(J, il, im, k);
+        } else {
+            float2 s = make_float2(0.f, 0.f);
+            for (int l = 0; l <= k; ++l) cfma(s, J.Li32[(size_t)l * p + k], steer(J, il, im, l));
+            c[k] = s;
+        }
+    }
+}
+
+// Adjoint over a list of cached vectors: t_j = Re(c_j^H U c_j), handed to
+// epi(j, t_j) on threads < kTile.
+template <class Epi>
+__device__ void adjoint_list(const JobDev &J, const float2 *U, const int *pos, int n, float2 *A,
+                             float *red, Epi epi) {
+    for (int j0 = 0; j0 < n; j0 += kTile) {
+        const int np = min(kTile, n - j0);
+        fill_cache_adj(J, pos, j0, np, A);
+        __syncthreads();
+        adj_chunk(U, J.p, A, red);
+        if (threadIdx.x < np) epi(j0 + threadIdx.x, red[threadIdx.x]);
+        __syncthreads();
+    }
+}
+
+// LSQR (Paige-Saunders) on the free set: min || b - M_F x ||, with
+// M_F x = vect(sum_j s_j x_j c_j c_j^H) and (M_F^H u)_j = s_j Re(c_j^H U c_j).
+// b is in J.W0 on entry.  The bidiagonalisation follows eq. initbeta ..
+// eq. lanczos; rotations and stopping tests as in the FP64 oracle, scalars
+// in FP64.  Returns the iteration count; the solution is in J.xs[0..f).
+__device__ int lsqr_cta(const JobDev &J, int f, float2 *A, SolveShared &S) {
+    const int p = J.p, pp = p * p;
+    float2 *u = J.W0;
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < pp; e += blockDim.x) acc += (double)u[e].x * u[e].x + (double)u[e].y * u[e].y;
+    double beta = sqrt(block_sum(acc, S.dbuf));
+    const double bnorm = beta;
+    for (int j = threadIdx.x; j < f; j += blockDim.x) J.xs[j] = 0.f;
+    if (beta == 0.0) { __syncthreads(); return 0; }
+    {
+        const float ib = (float)(1.0 / beta);
+        for (int e = threadIdx.x; e < pp; e += blockDim.x) u[e] = make_float2(u[e].x * ib, u[e].y * ib);
+    }
+    __syncthreads();
+    const int *fpos = J.fpos;
+    adjoint_list(J, u, fpos, f, A, S.red, [&](int j, float t) {
+        J.v[j] = J.scale[J.supp[fpos[j]]] * t;
+    });
+    acc = 0.0;
+    for (int j = threadIdx.x; j < f; j += blockDim.x) acc += (double)J.v[j] * J.v[j];
+    double alpha = sqrt(block_sum(acc, S.dbuf));
+    if (alpha == 0.0) return 0;
+    {
+        const float ia = (float)(1.0 / alpha);
+        for (int j = threadIdx.x; j < f; j += blockDim.x) {
+            J.v[j] *= ia;
+            J.w[j] = J.v[j];
+        }
+    }
+    __syncthreads();
+    double phibar = beta, rhobar = alpha, anorm2 = 0.0;
+    const int maxit = J.lsqr_maxit > 0 ? J.lsqr_maxit : 4 * f + 20;
+    int it = 0;
+    float *wt = J.xs + J.cap;   // weight scratch (cap floats after xs)
+    for (it = 1; it <= maxit; ++it) {
+        // u <- M v - alpha u
+        for (int j = threadIdx.x; j < f; j += blockDim.x) wt[j] = J.scale[J.supp[fpos[j]]] * J.v[j];
+        __syncthreads();
+        forward_list(J, fpos, wt, f, false, nullptr, false, J.W1, A, S.wsm);
+        acc = 0.0;
+        const float fa = (float)alpha;
+        for (int e = threadIdx.x; e < pp; e += blockDim.x) {
+            const float2 mv = J.W1[e];
+            const float2 t = make_float2(mv.x - fa * u[e].x, mv.y - fa * u[e].y);
+            u[e] = t;
+            acc += (double)t.x * t.x + (double)t.y * t.y;
+        }
+        beta = sqrt(block_sum(acc, S.dbuf));
+        if (beta > 0.0) {
+            const float ib = (float)(1.0 / beta);
+            for (int e = threadIdx.x; e < pp; e += blockDim.x) u[e] = make_float2(u[e].x * ib, u[e].y * ib);
+        }
+        __syncthreads();
+        anorm2 += alpha * alpha + beta * beta;
+        // v <- M^H u - beta v
+        const float fb = (float)beta;
+        adjoint_list(J, u, fpos, f, A, S.red, [&](int j, float t) {
+            J.v[j] = J.scale[J.supp[fpos[j]]] * t - fb * J.v[j];
+        });
+        acc = 0.0;
+        for (int j = threadIdx.x; j < f; j += blockDim.x) acc += (double)J.v[j] * J.v[j];
+        alpha = sqrt(block_sum(acc, S.dbuf));
+        if (alpha > 0.0) {
+            const float ia = (float)(1.0 / alpha);
+            for (int j = threadIdx.x; j < f; j += blockDim.x) J.v[j] *= ia;
+        }
+        __syncthreads();
+        // plane rotation
+        const double rho = hypot(rhobar, beta);
+        const double c = rhobar / rho, s = beta / rho;
+        const double theta = s * alpha;
+        rhobar = -c * alpha;
+        const double phi = c * phibar;
+        phibar = s * phibar;
+        const float t1 = (float)(phi / rho), t2 = (float)(-theta / rho);
+        acc = 0.0;
+        for (int j = threadIdx.x; j < f; j += blockDim.x) {
+            const float xj = J.xs[j] + t1 * J.w[j];
+            J.xs[j] = xj;
+            J.w[j] = J.v[j] + t2 * J.w[j];
+            acc += (double)xj * xj;
+        }
+        const double xnorm = sqrt(block_sum(acc, S.dbuf));
+        const double rnorm = phibar;
+        const double arnorm = phibar * alpha * fabs(c);
+        const double anorm = sqrt(anorm2);
+        if (rnorm <= J.lsqr_btol * bnorm + J.lsqr_atol * anorm * xnorm) break;
+        if (arnorm <= J.lsqr_atol * anorm * rnorm) break;
+    }
+    return min(it, maxit);
+}
+
+__device__ __forceinline__ double flops_fwd(int p, int n) { return 4.0 * p * (double)p * n; }
+__device__ __forceinline__ double flops_adj(int p, int n) { return 8.0 * p * (double)p * n; }
+
+// Remove support slot sl (pixel i) by moving the last entry into it.
+__device__ void supp_remove(const JobDev &J, int i, int &ns) {
+    const int p = J.p;
+    const int sl = J.slot[i];
+    const int last = ns - 1;
+    if (sl != last) {
+        const int moved = J.supp[last];
+        for (int k = threadIdx.x; k < p; k += blockDim.x)
+            J.cvec[(size_t)sl * p + k] = J.cvec[(size_t)last * p + k];
+        if (threadIdx.x == 0) {
+            J.supp[sl] = moved;
+            J.slot[moved] = sl;
+        }
+    }
+    if (threadIdx.x == 0) J.slot[i] = -1;
+    ns = last;
+    __syncthreads();
+}
+
+// Persistent active-set driver (Table I), one CTA per job.
+__global__ void __launch_bounds__(kThreads, 1)
+k_solve(JobDev *const *jobs, DevInfo *batch_info, double *const *sigma_out) {
+    const JobDev &J = *jobs[blockIdx.x];
+    extern __shared__ float4 smem4[];
+    float2 *A = reinterpret_cast<float2 *>(smem4);
+    __shared__ SolveShared S;
+    DevInfo info{};
+    info.status = IMG_OK;
+    if (J.flags[0] != 0 || J.flags[1] != 1) {
+        info.status = J.flags[0] != 0 ? J.flags[0] : IMG_EINVAL;
+        if (threadIdx.x == 0) {
+            *J.info = info;
+            if (batch_info) batch_info[blockIdx.x] = info;
+        }
+        return;
+    }
+    const int p = J.p, Q = J.Q;
+    const bool pwls = J.cost == IMG_COST_PWLS;
+    for (int i = threadIdx.x; i < Q; i += blockDim.x) {
+        J.x[i] = 0.0;
+        J.set[i] = IMG_SET_L;
+        J.slot[i] = -1;
+        J.grad[i] = 0.f;
+    }
+    __syncthreads();
+    int ns = 0;           // support size |F u U|
+    bool flag = true;     // Freegradient-isnotzero
+    int imin = -1;
+    double lam_min = 0.0;
+    const int max_outer = J.max_outer > 0 ? J.max_outer : 10 * Q + 100;
+    int outer = 0;
+    bool converged = false;
+    float *wt = J.xs + J.cap;
+    while (outer < max_outer) {
+        ++outer;
+        if (flag) {
+            const int f = block_compact(ns, [&](int pos) { return J.set[J.supp[pos]] == IMG_SET_F; },
+                                        J.fpos, S.cbuf);
+            bool feasible = true;
+            if (f > 0) {
+                // b = B0 - sum_{U} s_i x_i c_i c_i^H   (eq. bsubproblemLS / MVDR)
+                const int nu = block_compact(ns, [&](int pos) { return J.set[J.supp[pos]] == IMG_SET_U; },
+                                             J.fpos + f, S.cbuf);
+                for (int j = threadIdx.x; j < nu; j += blockDim.x) {
+                    const int i = J.supp[J.fpos[f + j]];
+                    wt[j] = -J.scale[i] * (float)J.x[i];
+                }
+                __syncthreads();
+                forward_list(J, J.fpos + f, wt, nu, false, pwls ? nullptr : J.R32, pwls, J.W0, A, S.wsm);
+                info.op_flops += flops_fwd(p, nu);
+                const int its = lsqr_cta(J, f, A, S);
+                info.lsqr_iters += its;
+                info.op_flops += (its + 1) * (flops_fwd(p, f) + flops_adj(p, f));
+                int bad = 0;
+                for (int j = threadIdx.x; j < f; j += blockDim.x) {
+                    const double z = J.xs[j];
+                    const int i = J.supp[J.fpos[j]];
+                    if (!(z >= 0.0 && z <= J.upper[i])) bad = 1;
+                }
+                feasible = __syncthreads_or(bad) == 0;
+            }
+            if (feasible) {
+                for (int j = threadIdx.x; j < f; j += blockDim.x) J.x[J.supp[J.fpos[j]]] = (double)J.xs[j];
+                flag = false;
+                __syncthreads();
+                // gradient: E = B0 - sum_S s_i x_i c_i c_i^H, U_g = T^H E T
+                for (int j = threadIdx.x; j < ns; j += blockDim.x) {
+                    const int i = J.supp[j];
+                    wt[j] = -J.scale[i] * (float)J.x[i];
+                }
+                __syncthreads();
+                forward_list(J, nullptr, wt, ns, false, pwls ? nullptr : J.R32, pwls, J.W1, A, S.wsm);
+                info.op_flops += flops_fwd(p, ns);
+                const float2 *Ug = J.W1;
+                if (pwls) {
+                    cgemm_pp(p, J.W1, false, J.Li32, J.W2);
+                    cgemm_pp(p, J.Li32, true, J.W2, J.W0);
+                    Ug = J.W0;
+                }
+                double best = INFINITY;
+                int bidx = 0x7fffffff;
+                const int ntiles = (Q + kTile - 1) / kTile;
+                for (int t = 0; t < ntiles; ++t) {
+                    const int pix0 = t * kTile;
+                    const int np = min(kTile, Q - pix0);
+                    fill_steer_adj(J, pix0, np, A);
+                    __syncthreads();
+                    adj_chunk(Ug, p, A, S.red);
+                    if (threadIdx.x < np) {
+                        const int i = pix0 + threadIdx.x;
+                        const float g = -J.scale[i] * S.red[threadIdx.x];
+                        J.grad[i] = g;
+                        const unsigned char st = J.set[i];
+                        if (st != IMG_SET_F) {
+                            const double lam = st == IMG_SET_U ? -(double)g : (double)g;
+                            if (lam < -(double)J.eps[i] && (lam < best || (lam == best && i < bidx))) {
+                                best = lam;
+                                bidx = i;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+                info.op_flops += flops_adj(p, Q);
+                block_argmin(best, bidx, S.vbuf, S.ibuf);
+                lam_min = best;
+                if (bidx == 0x7fffffff) {
+                    converged = true;
+                    break;
+                }
+                imin = bidx;
+            } else {
+                // step towards z: mu_i per eq. mumax, smallest index on ties
+                double best = INFINITY;
+                int bidx = 0x7fffffff;
+                for (int j = threadIdx.x; j < f; j += blockDim.x) {
+                    const int i = J.supp[J.fpos[j]];
+                    const double xi = J.x[i];
+                    const double pd = (double)J.xs[j] - xi;
+                    double mu = INFINITY;
+                    if (pd > 0.0) mu = (J.upper[i] - xi) / pd;
+                    else if (pd < 0.0) mu = -xi / pd;
+                    if (mu < best || (mu == best && i < bidx)) { best = mu; bidx = i; }
+                }
+                block_argmin(best, bidx, S.vbuf, S.ibuf);
+                const double mu = best;
+                const int ic = bidx;
+                // the blocking pixel moves to U when its direction is positive
+                int dirup = 0;
+                for (int j = threadIdx.x; j < f; j += blockDim.x)
+                    if (J.supp[J.fpos[j]] == ic) dirup = ((double)J.xs[j] - J.x[ic] > 0.0) ? 1 : 0;
+                const bool up = __syncthreads_or(dirup) != 0;
+                for (int j = threadIdx.x; j < f; j += blockDim.x) {
+                    const int i = J.supp[J.fpos[j]];
+                    const double xi = J.x[i];
+                    J.x[i] = xi + mu * ((double)J.xs[j] - xi);
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    J.set[ic] = up ? IMG_SET_U : IMG_SET_L;
+                    J.x[ic] = up ? J.upper[ic] : 0.0;
+                }
+                __syncthreads();
+                if (!up) supp_remove(J, ic, ns);
+                flag = true;
+            }
+        } else {
+            // delete a constraint: pixel imin joins F at its current value
+            const int i = imin;
+            if (J.slot[i] < 0) {
+                if (ns >= J.cap) {
+                    info.status = IMG_ENOMEM;
+                    break;
+                }
+                cache_vector(J, i, ns);
+                if (threadIdx.x == 0) {
+                    J.supp[ns] = i;
+                    J.slot[i] = ns;
+                }
+                ++ns;
+            }
+            if (threadIdx.x == 0) J.set[i] = IMG_SET_F;
+            __syncthreads();
+            flag = true;
+        }
+    }
+    if (!converged && info.status == IMG_OK) info.status = IMG_ENOTCONV;
+    double *out = sigma_out ? sigma_out[blockIdx.x] : nullptr;
+    int nf = 0, nu = 0;
+    for (int i = threadIdx.x; i < Q; i += blockDim.x) {
+        const double s = (double)J.scale[i] * J.x[i];
+        J.sigma[i] = s;
+        if (out) out[i] = s;
+        nf += J.set[i] == IMG_SET_F;
+        nu += J.set[i] == IMG_SET_U;
+    }
+    const double tf = block_sum((double)nf, S.dbuf);
+    const double tu = block_sum((double)nu, S.dbuf);
+    if (threadIdx.x == 0) {
+        info.outer = outer;
+        info.n_free = (int)tf;
+        info.n_upper = (int)tu;
+        info.converged = converged ? 1 : 0;
+        info.lambda_min = lam_min;
+        *J.info = info;
+        if (batch_info) batch_info[blockIdx.x] = info;
+    }
+}
+
+// ---------------------------------------------------------------- operators
+// K = sum_i x_i a_i a_i^H over all pixels, split over CTAs into partial
+// matrices part[b] (p x p each), then summed in order by k_psi_reduce.
+__global__ void k_psi_partial(const JobDev *Jp, const float *wx, float2 *part, int per_cta) {
+    extern __shared__ float4 smem4[];
+    float2 *C = reinterpret_cast<float2 *>(smem4);
+    __shared__ float wsm[kTile];
+    const JobDev &J = *Jp;
+    const int i0 = blockIdx.x * per_cta;
+    const int n = max(0, min(per_cta, J.Q - i0));
+    const int p = J.p;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float2 *K = part + (size_t)blockIdx.x * p * p;
+    for (int mt = 0; mt < p; mt += kTile) {
+        for (int nt = 0; nt < p; nt += kTile) {
+            const int r0 = mt + ty * 4, c0 = nt + tx * 4;
+            float2 acc[4][4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = make_float2(0.f, 0.f);
+            for (int j0 = 0; j0 < n; j0 += kTile) {
+                const int np = min(kTile, n - j0);
+                for (int e = threadIdx.x; e < kTile * p; e += kThreads) {
+                    const int j = e / p, k = e - j * p;
+                    float2 c = make_float2(0.f, 0.f);
+                    if (j < np) {
+                        const int i = i0 + j0 + j;
+                        const int im = i / J.n_l, il = i - im * J.n_l;
+                        c = steer(J, il, im, k);
+                    }
+                    C[e] = c;
+                }
+                if (threadIdx.x < kTile) wsm[threadIdx.x] = threadIdx.x < np ? wx[i0 + j0 + threadIdx.x] : 0.f;
+                __syncthreads();
+                if (r0 < p && c0 < p) {
+                    for (int j = 0; j < np; ++j) {
+                        const float wj = wsm[j];
+                        const float2 *cj = C + j * p;
+                        float2 ck[4], cl[4];
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) {
+                            const float2 t = (r0 + r < p) ? cj[r0 + r] : make_float2(0.f, 0.f);
+                            ck[r] = make_float2(wj * t.x, wj * t.y);
+                        }
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const float2 t = (c0 + c < p) ? cj[c0 + c] : make_float2(0.f, 0.f);
+                            cl[c] = make_float2(t.x, -t.y);
+                        }
+#pragma unroll
+                        for (int r = 0; r < 4; ++r)
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) cfma(acc[r][c], ck[r], cl[c]);
+                    }
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int k = r0 + r, l = c0 + c;
+                    if (k < p && l < p) K[(size_t)l * p + k] = acc[r][c];
+                }
+        }
+    }
+}
+
+__global__ void k_psi_reduce(const float2 *part, int nparts, int pp, double2 *Kout) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < pp; e += gridDim.x * blockDim.x) {
+        double sx = 0.0, sy = 0.0;
+        for (int b = 0; b < nparts; ++b) {
+            const float2 v = part[(size_t)b * pp + e];
+            sx += v.x;
+            sy += v.y;
+        }
+        Kout[e] = make_double2(sx, sy);
+    }
+}
+
+__global__ void k_psi_adj(const JobDev *J, const float2 *U, double *out) {
+    // out_i = Re(a_i^H U a_i) over all pixels (Psi^H vect(U))
+    extern __shared__ float4 smem4[];
+    float2 *A = reinterpret_cast<float2 *>(smem4);
+    float *red = reinterpret_cast<float *>(A + J->p * kTile);
+    const int ntiles = (J->Q + kTile - 1) / kTile;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int pix0 = t * kTile;
+        const int np = min(kTile, J->Q - pix0);
+        fill_steer_adj(*J, pix0, np, A);
+        __syncthreads();
+        adj_chunk(U, J->p, A, red);
+        if (threadIdx.x < np) out[pix0 + threadIdx.x] = red[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+__global__ void k_to_double(const float *src, double *dst, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i];
+}
+
+__global__ void k_z2c(const double2 *src, float2 *dst, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        dst[i] = make_float2((float)src[i].x, (float)src[i].y);
+}
+
+__global__ void k_c2z(const float2 *src, double2 *dst, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        dst[i] = make_double2(src[i].x, src[i].y);
+}
+
+__global__ void k_d2f(const double *src, float *dst, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = (float)src[i];
+}
+
+// ---------------------------------------------------------------- launchers
+size_t solve_smem_bytes(int p) { return (size_t)p * kTile * sizeof(float2); }
+size_t bounds_smem_bytes(int p) {
+    return (size_t)p * kTile * sizeof(float2) + (kTile + 16 * kTile) * sizeof(float);
+}
+
+static int g_num_sms = 0;
+static int num_sms() {
+    if (!g_num_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 1;
+    }
+    return g_num_sms;
+}
+
+cudaError_t launch_tables(JobDev *const *jobs, int n, cudaStream_t st) {
+    k_tables<<<dim3(16, n), kThreads, 0, st>>>(jobs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_factor(JobDev *const *jobs, int n, cudaStream_t st) {
+    k_factor<<<n, kThreads, 0, st>>>(jobs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bounds(JobDev *const *jobs, int n, int max_tiles, int max_p, cudaStream_t st) {
+    const size_t sm = bounds_smem_bytes(max_p);
+    cudaError_t e = cudaFuncSetAttribute(k_bounds, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int per_job = (2 * num_sms() + n - 1) / n;
+    per_job = max(1, min(per_job, max_tiles));
+    k_bounds<<<dim3(per_job, n), kThreads, sm, st>>>(jobs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(JobDev *const *jobs, int n, cudaStream_t st) {
+    k_finalize<<<n, kThreads, 0, st>>>(jobs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve(JobDev *const *jobs, int n, int max_p, DevInfo *batch_info,
+                         double *const *sigma_out, cudaStream_t st) {
+    const size_t sm = solve_smem_bytes(max_p);
+    cudaError_t e = cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_solve<<<n, kThreads, sm, st>>>(jobs, batch_info, sigma_out);
+    return cudaGetLastError();
+}
+
+// Psi x over all pixels: nparts CTAs write partial p x p sums into `part`
+// (nparts * p * p float2 of scratch), reduced in a fixed order in FP64.
+cudaError_t launch_psi(const JobDev *job_dev, const float *wx, float2 *part, int nparts, int Q,
+                       int p, double2 *Kout, cudaStream_t st) {
+    const size_t sm = (size_t)p * kTile * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(k_psi_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int per = (Q + nparts - 1) / nparts;
+    per = ((per + kTile - 1) / kTile) * kTile;
+    const int used = (Q + per - 1) / per;
+    k_psi_partial<<<used, kThreads, sm, st>>>(job_dev, wx, part, per);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_psi_reduce<<<(p * p + 255) / 256, 256, 0, st>>>(part, used, p * p, Kout);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_psi_adj(const JobDev *job_dev, const float2 *U, double *out, int Q, int p,
+                           cudaStream_t st) {
+    const size_t sm = bounds_smem_bytes(p);
+    cudaError_t e = cudaFuncSetAttribute(k_psi_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const int ntiles = (Q + kTile - 1) / kTile;
+    k_psi_adj<<<min(ntiles, 2 * num_sms()), kThreads, sm, st>>>(job_dev, U, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_z2c(const double2 *src, float2 *dst, int n, cudaStream_t st) {
+    k_z2c<<<min(1024, (n + 255) / 256 + 1), 256, 0, st>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_c2z(const float2 *src, double2 *dst, int n, cudaStream_t st) {
+    k_c2z<<<min(1024, (n + 255) / 256 + 1), 256, 0, st>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_d2f(const double *src, float *dst, int n, cudaStream_t st) {
+    k_d2f<<<min(1024, (n + 255) / 256 + 1), 256, 0, st>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_double(const float *src, double *dst, int n, cudaStream_t st) {
+    k_to_double<<<min(1024, (n + 255) / 256 + 1), 256, 0, st>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+}  // namespace img
