@@ -30,7 +30,8 @@
  *     keeps and never frees caller memory.
  *   - Calls on one context are not thread-safe; separate contexts are
  *     independent.  Every call returns after its results are in the
- *     caller's buffer (it synchronises the context's stream).
+ *     caller's buffer (it synchronises the context's stream), except
+ *     img_set_covariance with on_device = 1, which only enqueues the copy.
  *   - No C++ exception crosses this boundary; failures are status codes.
  */
 #ifndef IMG_GB300_H
@@ -65,7 +66,7 @@ enum { IMG_SET_L = 0, IMG_SET_U = 1, IMG_SET_F = 2 };  /* pixel sets (Sec. IV-A)
 
 /*
  * Problem description.  img_create copies every field and array.
- *   p        antennas, 2 <= p <= 512
+ *   p        antennas, 2 <= p <= 384
  *   n_l,n_m  grid size, Q = n_l * n_m <= 2^24
  *   ant_xyz  host, p x 3 row-major (x_k, y_k, z_k) in units of the reference
  *            wavelength.  z_k must be 0 (planar array): the separable
@@ -131,7 +132,9 @@ img_status img_create(const img_params *prm, img_ctx **out);
  *   N      number of samples; must exceed p (R_hat singular otherwise and
  *          C undefined) -> else IMG_EINVAL
  * Host input is checked for finite, Hermitian (relative 1e-6) values with a
- * positive real diagonal.  Previous bounds and images are invalidated.  The
+ * positive real diagonal; device input is copied asynchronously on the
+ * context's stream (the caller keeps it alive until the next call on this
+ * context returns).  Previous bounds and images are invalidated.  The
  * Cholesky factor is computed on the device at the next call that needs it;
  * a non-PD R_hat then makes that call return IMG_ENOTPD. */
 img_status img_set_covariance(img_ctx *ctx, const void *R, int dtype,
@@ -142,9 +145,9 @@ img_status img_set_covariance(img_ctx *ctx, const void *R, int dtype,
  * IMG_ENOTPD. */
 img_status img_dirty(img_ctx *ctx, double *out, int on_device);
 
-/* Upper bound gamma used by the solver (Sec. III-D): for IMG_BOUND_MVDR
- * C / (a_i^H R_hat^-1 a_i) (eq. wmvdr and the unbiased form with C),
- * for IMG_BOUND_MF the dirty image, each inflated as configured. */
+/* MVDR upper bound C / (a_i^H R_hat^-1 a_i) (eq. wmvdr with K = 1 and the
+ * unbiased form with C, Sec. III-D), inflated as configured, into
+ * out[0..Q).  It is the solver's gamma when bound = IMG_BOUND_MVDR. */
 img_status img_mvdr_bound(img_ctx *ctx, double *out, int on_device);
 
 /* Bounded least-squares image (Table I with LSQR subproblems) into
@@ -169,6 +172,12 @@ img_status img_psi(img_ctx *ctx, const double *x, double *Kout, int on_device);
 /* Adjoint operator (Psi^H vect(U))_i = Re(a_i^H U a_i) (Sec. V-B):
  * U p x p Hermitian complex128 column-major -> out[0..Q) double. */
 img_status img_psi_adj(img_ctx *ctx, const double *U, double *out, int on_device);
+
+/* Factor R_hat, dirty images and bounds of several jobs in single launches
+ * (the step img_solve_batch would otherwise run first).  Every context must
+ * hold a covariance and use the same device; runs on ctxs[0]'s stream.
+ * Returns the first job's IMG_ENOTPD if any factorisation failed. */
+img_status img_prepare_batch(img_ctx *const *ctxs, int n);
 
 /* Batch of independent jobs in single launches (the paper has no batching;
  * jobs are independent, Sec. V-B).  Every context must hold a covariance and

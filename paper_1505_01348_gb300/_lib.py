@@ -23,7 +23,8 @@ SET_L, SET_U, SET_F = 0, 1, 2
 
 EXPORTS = ("img_params_default", "img_create", "img_set_covariance", "img_dirty",
            "img_mvdr_bound", "img_solve", "img_get_sets", "img_get_gradient", "img_psi",
-           "img_psi_adj", "img_solve_batch", "img_destroy", "img_status_str")
+           "img_psi_adj", "img_prepare_batch", "img_solve_batch", "img_destroy",
+           "img_status_str")
 
 
 class ImgParams(C.Structure):
@@ -90,6 +91,8 @@ def load(build_if_missing: bool = False) -> C.CDLL:
     lib.img_psi.restype = i
     lib.img_psi_adj.argtypes = [vp, dp, dp, i]
     lib.img_psi_adj.restype = i
+    lib.img_prepare_batch.argtypes = [C.POINTER(vp), i]
+    lib.img_prepare_batch.restype = i
     lib.img_solve_batch.argtypes = [C.POINTER(vp), i, C.POINTER(dp), C.POINTER(SolveInfo), i]
     lib.img_solve_batch.restype = i
     lib.img_destroy.argtypes = [vp]
@@ -231,6 +234,14 @@ class Imager:
         out = np.empty(self.Q, dtype=np.float64)
         _check(self._lib.img_psi_adj(self.h, U.ctypes.data, out.ctypes.data, 0), "img_psi_adj")
         return out
+
+
+def prepare_batch(imagers):
+    """Factor and bound several jobs in single launches."""
+    lib = load()
+    n = len(imagers)
+    hs = (C.c_void_p * n)(*[im.h.value for im in imagers])
+    _check(lib.img_prepare_batch(hs, n), "img_prepare_batch")
 
 
 def solve_batch(imagers, outs=None, allow=(IMG_ENOTCONV,)):

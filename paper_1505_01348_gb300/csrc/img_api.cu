@@ -128,7 +128,7 @@ img_status prepare(img_ctx *c) {
     CK(img::launch_factor(c->djp, 1, c->stream));
     const int ntiles = (c->hj.Q + img::kTile - 1) / img::kTile;
     CK(img::launch_bounds(c->djp, 1, ntiles, c->prm.p, c->stream));
-    CK(img::launch_finalize(c->djp, 1, c->stream));
+    CK(img::launch_finalize(c->djp, 1, c->stream, nullptr));
     int flag = 0;
     CK(cudaMemcpyAsync(&flag, c->hj.flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -160,6 +160,7 @@ struct BatchWs {
     JobDev **jobs = nullptr;
     DevInfo *infos = nullptr;
     double **sig = nullptr;
+    int *status = nullptr;
 };
 BatchWs g_ws;
 
@@ -171,13 +172,14 @@ img_status ws_reserve(int n, int device) {
     }
     int cap = 64;
     while (cap < n) cap *= 2;
-    size_t bytes = cap * (sizeof(JobDev *) + sizeof(DevInfo) + sizeof(double *)) + 512;
+    size_t bytes = cap * (sizeof(JobDev *) + sizeof(DevInfo) + sizeof(double *) + sizeof(int)) + 1024;
     char *b = nullptr;
     CK(cudaMalloc(&b, bytes));
     g_ws.jobs = reinterpret_cast<JobDev **>(b);
     g_ws.sig = reinterpret_cast<double **>(b + cap * sizeof(JobDev *));
     g_ws.infos = reinterpret_cast<DevInfo *>(
         b + ((cap * (sizeof(JobDev *) + sizeof(double *)) + 255) & ~size_t(255)));
+    g_ws.status = reinterpret_cast<int *>(reinterpret_cast<char *>(g_ws.infos) + cap * sizeof(DevInfo));
     g_ws.cap = cap;
     g_ws.device = device;
     return IMG_OK;
@@ -363,11 +365,13 @@ img_status img_set_covariance(img_ctx *c, const void *R, int dtype, long long N,
             CK(img::launch_c2z(static_cast<const float2 *>(R), c->hj.R64, (int)pp, c->stream));
         }
     }
+    // N and the cleared factor/bounds flags; pageable sources are staged by
+    // the runtime before cudaMemcpyAsync returns, so locals are safe here.
     c->hj.N = N;
-    int init_flags[2] = {-1, 0};
     CK(cudaMemcpyAsync(&c->dj->N, &c->hj.N, sizeof(long long), cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->hj.flags, init_flags, sizeof(init_flags), cudaMemcpyHostToDevice, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemsetAsync(c->hj.flags, 0xff, sizeof(int), c->stream));
+    CK(cudaMemsetAsync(c->hj.flags + 1, 0, sizeof(int), c->stream));
+    if (!on_device) CK(cudaStreamSynchronize(c->stream));
     c->has_cov = true;
     return IMG_OK;
 }
@@ -439,6 +443,41 @@ img_status img_psi_adj(img_ctx *c, const double *U, double *out, int on_device) 
     return copy_out_double(c, c->outd, out, Q, 0);
 }
 
+img_status img_prepare_batch(img_ctx *const *ctxs, int n) {
+    if (!ctxs || n <= 0) return IMG_EINVAL;
+    for (int j = 0; j < n; ++j) {
+        if (!ctxs[j] || !ctxs[j]->has_cov) return IMG_EINVAL;
+        if (ctxs[j]->device != ctxs[0]->device) return IMG_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(g_ws.mu);
+    img_status st = ws_reserve(n, ctxs[0]->device);
+    if (st != IMG_OK) return st;
+    cudaStream_t s = ctxs[0]->stream;
+    for (int j = 0; j < n; ++j)
+        if (ctxs[j]->stream != s) CK(cudaStreamSynchronize(ctxs[j]->stream));
+    std::vector<JobDev *> ptrs(n);
+    int max_p = 0, max_tiles = 1;
+    for (int j = 0; j < n; ++j) {
+        ptrs[j] = ctxs[j]->dj;
+        max_p = std::max(max_p, ctxs[j]->prm.p);
+        max_tiles = std::max(max_tiles, (ctxs[j]->hj.Q + img::kTile - 1) / img::kTile);
+    }
+    CK(cudaMemcpyAsync(g_ws.jobs, ptrs.data(), n * sizeof(JobDev *), cudaMemcpyHostToDevice, s));
+    CK(img::launch_factor(g_ws.jobs, n, s));
+    CK(img::launch_bounds(g_ws.jobs, n, max_tiles, max_p, s));
+    CK(img::launch_finalize(g_ws.jobs, n, s, g_ws.status));
+    std::vector<int> flags(n);
+    CK(cudaMemcpyAsync(flags.data(), g_ws.status, n * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    img_status first = IMG_OK;
+    for (int j = 0; j < n; ++j) {
+        ctxs[j]->prepared = true;
+        ctxs[j]->prep_status = flags[j] == 0 ? IMG_OK : IMG_ENOTPD;
+        if (first == IMG_OK && flags[j] != 0) first = IMG_ENOTPD;
+    }
+    return first;
+}
+
 img_status img_solve_batch(img_ctx *const *ctxs, int n, double *const *sigma, img_solve_info *infos,
                            int on_device) {
     if (!ctxs || n <= 0 || !sigma) return IMG_EINVAL;
@@ -469,7 +508,7 @@ img_status img_solve_batch(img_ctx *const *ctxs, int n, double *const *sigma, im
         CK(cudaMemcpyAsync(g_ws.jobs, prep.data(), np * sizeof(JobDev *), cudaMemcpyHostToDevice, s));
         CK(img::launch_factor(g_ws.jobs, np, s));
         CK(img::launch_bounds(g_ws.jobs, np, max_tiles, max_p, s));
-        CK(img::launch_finalize(g_ws.jobs, np, s));
+        CK(img::launch_finalize(g_ws.jobs, np, s, nullptr));
     }
     CK(cudaMemcpyAsync(g_ws.jobs, ptrs.data(), n * sizeof(JobDev *), cudaMemcpyHostToDevice, s));
     if (on_device)

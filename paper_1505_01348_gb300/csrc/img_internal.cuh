@@ -73,7 +73,7 @@ cudaError_t launch_tables(JobDev *const *jobs, int n, cudaStream_t st);
 cudaError_t launch_factor(JobDev *const *jobs, int n, cudaStream_t st);
 cudaError_t launch_bounds(JobDev *const *jobs, int n, int max_tiles, int max_p,
                           cudaStream_t st);
-cudaError_t launch_finalize(JobDev *const *jobs, int n, cudaStream_t st);
+cudaError_t launch_finalize(JobDev *const *jobs, int n, cudaStream_t st, int *batch_status);
 cudaError_t launch_solve(JobDev *const *jobs, int n, int max_p, DevInfo *batch_info,
                          double *const *sigma_out, cudaStream_t st);
 cudaError_t launch_psi(const JobDev *job_dev, const float *wx, float2 *part, int nparts, int Q,

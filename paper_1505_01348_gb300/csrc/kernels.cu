@@ -146,8 +146,9 @@ __global__ void k_bounds(JobDev *const *jobs) {
 //   C = N/(N-p) or 1; mvdr = C/h; D = h^2/C; std_MF = dirty/sqrt(N);
 //   std_MVDR = mvdr/sqrt(N-p-1); gamma = chosen image, optionally inflated;
 //   PWLS: x = D sigma (scale 1/D, upper D gamma); eps = kappa std with a floor.
-__global__ void k_finalize(JobDev *const *jobs) {
+__global__ void k_finalize(JobDev *const *jobs, int *batch_status) {
     const JobDev &J = *jobs[blockIdx.x];
+    if (batch_status && threadIdx.x == 0) batch_status[blockIdx.x] = J.flags[0];
     if (J.flags[0] != 0) return;
     __shared__ double sbuf[kThreads / 32];
     const double C = J.bias_c ? (double)J.N / (double)(J.N - J.p) : 1.0;
@@ -691,8 +692,8 @@ cudaError_t launch_bounds(JobDev *const *jobs, int n, int max_tiles, int max_p, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(JobDev *const *jobs, int n, cudaStream_t st) {
-    k_finalize<<<n, kThreads, 0, st>>>(jobs);
+cudaError_t launch_finalize(JobDev *const *jobs, int n, cudaStream_t st, int *batch_status) {
+    k_finalize<<<n, kThreads, 0, st>>>(jobs, batch_status);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,53 @@
+"""Write FP64-oracle reference records for full-size parity tests.
+
+Each record stores the synthetic inputs (so the GPU test consumes exactly the
+covariance the oracle saw, independent of the platform's BLAS rounding) and
+the oracle's outputs.  Only synth/ and oracle/ are used here.
+
+    python tests/golden/make_golden.py mid_pwls
+"""
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import synth                       # noqa: E402
+from oracle import imager as O     # noqa: E402
+
+RECORDS = {
+    # 128x128 grid, p = 64 log-spiral, 20 points + Gaussian blob, N = 1e4,
+    # PWLS with the MVDR bound, kappa = 6 (the bench workload's image)
+    "mid_pwls": dict(maker=lambda: synth.mid(), prm=O.Params(cost=O.COST_PWLS, kappa=6.0,
+                                                                eps_floor=1e-6)),
+    "mid_ls": dict(maker=lambda: synth.mid(), prm=O.Params(cost=O.COST_LS, kappa=6.0,
+                                                            eps_floor=1e-6)),
+}
+
+
+def make(name: str) -> str:
+    rec = RECORDS[name]
+    job = rec["maker"]()
+    prm = rec["prm"]
+    t0 = time.time()
+    res = O.image_job(job, prm)
+    dt = time.time() - t0
+    out = os.path.join(HERE, f"{name}.npz")
+    np.savez_compressed(
+        out, ant_xyz=job.ant_xyz, l=job.l, m=job.m, lam=job.lam, R=job.R, N=job.N,
+        cost=prm.cost, kappa=prm.kappa, eps_floor=prm.eps_floor,
+        dirty=res.bounds.dirty, mvdr=res.bounds.mvdr, gamma=res.bounds.gamma,
+        sigma=res.solve.sigma, sets=res.solve.sets, outer=res.solve.outer,
+        lsqr_iters=res.solve.lsqr_iters, converged=res.solve.converged,
+        events=np.array([(0 if e[0] == "free" else 1, e[1], e[2] if len(e) > 2 else -1)
+                         for e in res.solve.events], dtype=np.int64),
+        oracle_seconds=dt)
+    return out
+
+
+if __name__ == "__main__":
+    for n in (sys.argv[1:] or list(RECORDS)):
+        print(make(n))
