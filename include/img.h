@@ -59,9 +59,13 @@ enum { IMG_INFLATE_NONE = 0,                           /* gamma = dirty         
        IMG_INFLATE_RATIO = 1,                          /* (1 + alpha) dirty      */
        IMG_INFLATE_STD = 2 };                          /* dirty + alpha std      */
 enum { IMG_C64 = 0, IMG_C128 = 1 };
-enum { IMG_PREC_FP32 = 0,       /* FP32 operators on CUDA cores              */
-       IMG_PREC_TF32X3 = 1,     /* split TF32 tensor-core operators          */
-       IMG_PREC_BF16X3 = 2 };   /* split BF16 tensor-core operators          */
+/* Arithmetic of the adjoint operator Psi^H (the dominant product).  The
+ * split forms run tcgen05 tensor-core MMAs on v = hi + lo 16-bit parts with
+ * FP32 accumulation (3 products); they apply when p <= 64 and fall back to
+ * FP32 CUDA cores otherwise. */
+enum { IMG_PREC_FP32 = 0,       /* FP32 on CUDA cores                        */
+       IMG_PREC_F16X3 = 1,      /* split FP16, power-of-two scaled: ~FP32    */
+       IMG_PREC_BF16X3 = 2 };   /* split BF16: ~16 significant bits          */
 enum { IMG_SET_L = 0, IMG_SET_U = 1, IMG_SET_F = 2 };  /* pixel sets (Sec. IV-A) */
 
 /*
@@ -85,6 +89,12 @@ enum { IMG_SET_L = 0, IMG_SET_U = 1, IMG_SET_F = 2 };  /* pixel sets (Sec. IV-A)
  *   lsqr_atol, lsqr_btol, lsqr_maxit  LSQR stopping rules (Paige-Saunders);
  *            maxit 0 means 4 f + 20 for f free pixels
  *   max_outer  cap on passes of the Table I loop (0: 10 Q + 100)
+ *   feas_tol  relative feasibility tolerance of the subproblem solution z:
+ *            -feas_tol u_i <= z_i <= (1 + feas_tol) u_i counts as feasible
+ *            and z is clipped into [0, u_i].  The paper gives no tolerance;
+ *            it matters because a lone free pixel's solution equals its
+ *            bound exactly (PWLS with the MVDR bound and C = 1, CLS with the
+ *            MF bound), so without one rounding decides the first test.
  *   precision  IMG_PREC_*
  *   support_cap  most pixels allowed off the lower bound at once (|F u U|);
  *            0 means min(Q, 16384).  Exceeding it ends the solve with
@@ -100,6 +110,7 @@ typedef struct {
     double alpha, kappa, eps_floor;
     double lsqr_atol, lsqr_btol;
     int lsqr_maxit, max_outer;
+    double feas_tol;
     int precision;
     int support_cap;
     void *stream;
@@ -116,10 +127,14 @@ typedef struct {
     double lambda_min;   /* smallest multiplier at the last gradient         */
     double op_flops;     /* algorithmic operator flops (Psi: 4p^2|S|,
                             Psi^H: 8p^2|S|) spent in this solve              */
+    double cyc_total;    /* SM clock cycles of the solve                     */
+    double cyc_gradient; /* ... of which in full-image gradients             */
+    double cyc_lsqr;     /* ... of which in LSQR subproblems                 */
 } img_solve_info;
 
 /* Fill *prm with defaults: PWLS, MVDR bound, C = 1, no inflation, kappa 6,
- * eps_floor 1e-6, LSQR atol = btol = 1e-6, maxit 0, max_outer 0, FP32. */
+ * eps_floor 1e-6, LSQR atol = btol = 1e-6, maxit 0, max_outer 0,
+ * feas_tol 1e-5, FP32. */
 void img_params_default(img_params *prm);
 
 /* Validate *prm, copy it, and allocate all device state for one job on the
@@ -164,6 +179,15 @@ img_status img_get_sets(img_ctx *ctx, unsigned char *sets);
 /* Gradient g (eq. gls or eq. gmvdr, in the solver variable) at the last
  * solve's final image into grad[0..Q), host memory. */
 img_status img_get_gradient(img_ctx *ctx, double *grad);
+
+/* Decisions of the last solve in order (Table I): events[k] encodes the
+ * kind in bits 24..25 (0: pixel freed, 1: pixel clamped to L, 2: clamped
+ * to U) and the pixel in bits 0..23; values[k] is the multiplier lambda_i
+ * of a freed pixel or the step mu_max of a clamp.  At most `capacity`
+ * entries are written (host memory); *count receives the total number of
+ * decisions, which may exceed what was recorded when the log filled. */
+img_status img_get_events(img_ctx *ctx, int *events, double *values, int capacity,
+                          int *count);
 
 /* Forward operator Psi x = vect(A diag(x) A^H) (notation section; Sec. V-B):
  * x[0..Q) real (double) -> Kout p x p complex128 column-major. */

@@ -139,6 +139,7 @@ class Params:
     lsqr_btol: float = 1e-12
     lsqr_maxit: int = 0          # 0 -> 4 f + 20
     max_outer: int = 0           # 0 -> 10 Q + 100 passes of the Table I loop
+    feas_tol: float = 0.0        # z within feas_tol * upper of a bound is feasible
 
 
 def bounds(A: np.ndarray, Psi: np.ndarray, R: np.ndarray, N: int,
@@ -327,7 +328,13 @@ def active_set(prob: CostProblem, eps: np.ndarray, prm: Params,
     Detection (Sec. IV-C): candidates are i in A with lambda_i < -eps_i; the
     candidate with the smallest lambda_i is freed, ties to the smallest index.
     mu ties go to the smallest pixel index; p_i = 0 gives mu_i = +inf.
-    Feasibility is non-strict: 0 <= z_i <= upper_i."""
+    Feasibility is non-strict: -tau u_i <= z_i <= (1 + tau) u_i with the
+    relative tolerance tau = feas_tol, and an accepted z is clipped into
+    [0, u_i].  The paper gives no tolerance; tau matters because the first
+    subproblem sits exactly on its bound: one free pixel gives z_i = h_i / C
+    against u_i = D_i gamma_i = h_i for PWLS with the MVDR bound (C = 1), and
+    z_i = gamma_i for CLS with the MF bound, so the untoleranced test is
+    decided by rounding."""
     M, b, up = prob.M, prob.b, prob.upper
     Q = M.shape[1]
     x = np.zeros(Q)
@@ -353,9 +360,10 @@ def active_set(prob: CostProblem, eps: np.ndarray, prm: Params,
                 z = res.x
             else:
                 z = np.zeros(0)
-            feasible = bool(np.all(z >= 0.0) and np.all(z <= up[F]))
+            tau = prm.feas_tol
+            feasible = bool(np.all(z >= -tau * up[F]) and np.all(z <= (1.0 + tau) * up[F]))
             if feasible:
-                x[F] = z
+                x[F] = np.clip(z, 0.0, up[F])
                 flag = False
                 g = gradient(prob, x)
                 lam = np.where(sets == SET_U, -g, g)

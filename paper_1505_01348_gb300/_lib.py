@@ -18,11 +18,12 @@ COST_LS, COST_PWLS = 0, 1
 BOUND_MF, BOUND_MVDR = 0, 1
 INFLATE_NONE, INFLATE_RATIO, INFLATE_STD = 0, 1, 2
 C64, C128 = 0, 1
-PREC_FP32, PREC_TF32X3, PREC_BF16X3 = 0, 1, 2
+PREC_FP32, PREC_F16X3, PREC_BF16X3 = 0, 1, 2
 SET_L, SET_U, SET_F = 0, 1, 2
 
 EXPORTS = ("img_params_default", "img_create", "img_set_covariance", "img_dirty",
-           "img_mvdr_bound", "img_solve", "img_get_sets", "img_get_gradient", "img_psi",
+           "img_mvdr_bound", "img_solve", "img_get_sets", "img_get_gradient", "img_get_events",
+           "img_psi",
            "img_psi_adj", "img_prepare_batch", "img_solve_batch", "img_destroy",
            "img_status_str")
 
@@ -34,14 +35,16 @@ class ImgParams(C.Structure):
                 ("cost", C.c_int), ("bound", C.c_int), ("bias_c", C.c_int), ("inflate", C.c_int),
                 ("alpha", C.c_double), ("kappa", C.c_double), ("eps_floor", C.c_double),
                 ("lsqr_atol", C.c_double), ("lsqr_btol", C.c_double),
-                ("lsqr_maxit", C.c_int), ("max_outer", C.c_int),
+                ("lsqr_maxit", C.c_int), ("max_outer", C.c_int), ("feas_tol", C.c_double),
                 ("precision", C.c_int), ("support_cap", C.c_int), ("stream", C.c_void_p)]
 
 
 class SolveInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("outer", C.c_int), ("lsqr_iters", C.c_int),
                 ("n_free", C.c_int), ("n_upper", C.c_int), ("converged", C.c_int),
-                ("lambda_min", C.c_double), ("op_flops", C.c_double)]
+                ("lambda_min", C.c_double), ("op_flops", C.c_double),
+                ("cyc_total", C.c_double), ("cyc_gradient", C.c_double),
+                ("cyc_lsqr", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -87,6 +90,8 @@ def load(build_if_missing: bool = False) -> C.CDLL:
     lib.img_get_sets.restype = i
     lib.img_get_gradient.argtypes = [vp, dp]
     lib.img_get_gradient.restype = i
+    lib.img_get_events.argtypes = [vp, dp, dp, i, C.POINTER(i)]
+    lib.img_get_events.restype = i
     lib.img_psi.argtypes = [vp, dp, dp, i]
     lib.img_psi.restype = i
     lib.img_psi_adj.argtypes = [vp, dp, dp, i]
@@ -222,6 +227,17 @@ class Imager:
         out = np.empty(self.Q, dtype=np.float64)
         _check(self._lib.img_get_gradient(self.h, out.ctypes.data), "img_get_gradient")
         return out
+
+    def events(self, capacity: int = 1 << 20):
+        """Decision log [(kind, pixel, value)], kind 0 free / 1 to L / 2 to U."""
+        n = C.c_int()
+        _check(self._lib.img_get_events(self.h, None, None, 0, C.byref(n)), "img_get_events")
+        m = min(n.value, capacity)
+        ev = np.empty(m, dtype=np.int32)
+        val = np.empty(m, dtype=np.float64)
+        _check(self._lib.img_get_events(self.h, ev.ctypes.data, val.ctypes.data, m, C.byref(n)),
+               "img_get_events")
+        return [(int(e) >> 24, int(e) & 0xFFFFFF, float(v)) for e, v in zip(ev, val)]
 
     def psi(self, x):
         x = np.ascontiguousarray(x, dtype=np.float64)

@@ -101,6 +101,9 @@ size_t carve(img_ctx *c, char *base) {
     J.W0 = cv.take<float2>(pp);
     J.W1 = cv.take<float2>(pp);
     J.W2 = cv.take<float2>(pp);
+    J.ev = cv.take<int>(J.ev_cap);
+    J.evv = cv.take<float>(J.ev_cap);
+    J.ev_count = cv.take<int>(1);
     J.info = cv.take<DevInfo>(1);
     J.flags = cv.take<int>(4);
     c->dj = cv.take<JobDev>(1);
@@ -111,6 +114,12 @@ size_t carve(img_ctx *c, char *base) {
     c->Z = cv.take<double2>(pp);
     c->outd = cv.take<double>(Q);
     return cv.off + 256;
+}
+
+// Arithmetic of the adjoint for one context: tensor cores when requested and
+// the 2p x 2p operand tiles fit in shared memory, CUDA cores otherwise.
+int mode_of(const img_ctx *c) {
+    return (c->prm.precision != IMG_PREC_FP32 && c->prm.p <= img::kMaxTcP) ? c->prm.precision : 0;
 }
 
 bool finite_all(const double *v, size_t n) {
@@ -127,7 +136,7 @@ img_status prepare(img_ctx *c) {
     if (c->prepared) return (img_status)c->prep_status;
     CK(img::launch_factor(c->djp, 1, c->stream));
     const int ntiles = (c->hj.Q + img::kTile - 1) / img::kTile;
-    CK(img::launch_bounds(c->djp, 1, ntiles, c->prm.p, c->stream));
+    CK(img::launch_bounds(c->djp, 1, ntiles, c->prm.p, mode_of(c), c->stream));
     CK(img::launch_finalize(c->djp, 1, c->stream, nullptr));
     int flag = 0;
     CK(cudaMemcpyAsync(&flag, c->hj.flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -194,6 +203,9 @@ void fill_info(img_solve_info *o, const DevInfo &d) {
     o->converged = d.converged;
     o->lambda_min = d.lambda_min;
     o->op_flops = d.op_flops;
+    o->cyc_total = d.cyc_total;
+    o->cyc_gradient = d.cyc_gradient;
+    o->cyc_lsqr = d.cyc_lsqr;
 }
 
 }  // namespace
@@ -213,6 +225,7 @@ void img_params_default(img_params *prm) {
     prm->eps_floor = 1e-6;
     prm->lsqr_atol = 1e-6;
     prm->lsqr_btol = 1e-6;
+    prm->feas_tol = 1e-5;
     prm->precision = IMG_PREC_FP32;
 }
 
@@ -245,6 +258,7 @@ img_status img_create(const img_params *prm, img_ctx **out) {
     if (!(P.kappa >= 0.0) || !(P.eps_floor >= 0.0) || !(P.alpha >= 0.0)) return IMG_EINVAL;
     if (!(P.lsqr_atol >= 0.0) || !(P.lsqr_btol >= 0.0) || P.lsqr_maxit < 0 || P.max_outer < 0)
         return IMG_EINVAL;
+    if (!(P.feas_tol >= 0.0) || !(P.feas_tol < 1.0)) return IMG_EINVAL;
     if (P.support_cap < 0) return IMG_EINVAL;
     if (!finite_all(P.ant_xyz, 3 * (size_t)P.p) || !finite_all(P.l, P.n_l) || !finite_all(P.m, P.n_m))
         return IMG_EINVAL;
@@ -285,6 +299,7 @@ img_status img_create(const img_params *prm, img_ctx **out) {
     J.lsqr_maxit = P.lsqr_maxit;
     J.max_outer = P.max_outer;
     J.cap = P.support_cap > 0 ? std::min(P.support_cap, Q) : std::min(Q, 16384);
+    J.ev_cap = (int)std::min<long long>(P.max_outer > 0 ? P.max_outer : 10LL * Q + 100, 1 << 20);
     J.precision = P.precision;
     J.alpha = P.alpha;
     J.kappa = P.kappa;
@@ -292,6 +307,7 @@ img_status img_create(const img_params *prm, img_ctx **out) {
     J.lam = P.lambda;
     J.lsqr_atol = P.lsqr_atol;
     J.lsqr_btol = P.lsqr_btol;
+    J.feas_tol = P.feas_tol;
     J.N = 0;
     {
         int sms = 1;
@@ -394,7 +410,7 @@ img_status img_solve(img_ctx *c, double *sigma, img_solve_info *info, int on_dev
     if (!c || !sigma) return IMG_EINVAL;
     img_status st = prepare(c);
     if (st != IMG_OK) return st;
-    CK(img::launch_solve(c->djp, 1, c->prm.p, nullptr, nullptr, c->stream));
+    CK(img::launch_solve(c->djp, 1, c->prm.p, mode_of(c), nullptr, nullptr, c->stream));
     DevInfo d{};
     CK(cudaMemcpyAsync(&d, c->hj.info, sizeof(DevInfo), cudaMemcpyDeviceToHost, c->stream));
     st = copy_out_double(c, c->hj.sigma, sigma, c->hj.Q, on_device);
@@ -413,6 +429,24 @@ img_status img_get_sets(img_ctx *c, unsigned char *sets) {
 img_status img_get_gradient(img_ctx *c, double *grad) {
     if (!c || !grad || !c->solved) return IMG_EINVAL;
     return copy_out_float(c, c->hj.grad, grad, c->hj.Q, 0);
+}
+
+img_status img_get_events(img_ctx *c, int *events, double *values, int capacity, int *count) {
+    if (!c || !count || capacity < 0 || !c->solved) return IMG_EINVAL;
+    int n = 0;
+    CK(cudaMemcpyAsync(&n, c->hj.ev_count, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *count = n;
+    const int m = std::min(std::min(n, capacity), c->hj.ev_cap);
+    if (m > 0 && events)
+        CK(cudaMemcpyAsync(events, c->hj.ev, m * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    if (m > 0 && values) {
+        std::vector<float> v(m);
+        CK(cudaMemcpyAsync(v.data(), c->hj.evv, m * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        for (int k = 0; k < m; ++k) values[k] = v[k];
+    }
+    return sync(c);
 }
 
 img_status img_psi(img_ctx *c, const double *x, double *Kout, int on_device) {
@@ -438,82 +472,130 @@ img_status img_psi_adj(img_ctx *c, const double *U, double *out, int on_device) 
     CK(cudaMemcpyAsync(c->Z, U, (size_t)p * p * sizeof(double2),
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     CK(img::launch_z2c(c->Z, c->U32, p * p, c->stream));
-    CK(img::launch_psi_adj(c->dj, c->U32, on_device ? out : c->outd, Q, p, c->stream));
+    CK(img::launch_psi_adj(c->dj, c->U32, on_device ? out : c->outd, Q, p, mode_of(c), c->stream));
     if (on_device) return sync(c);
     return copy_out_double(c, c->outd, out, Q, 0);
 }
 
-img_status img_prepare_batch(img_ctx *const *ctxs, int n) {
+}  // extern "C"
+
+namespace {
+
+// Jobs of a batch grouped by operator arithmetic (one launch per group):
+// order[] lists job indices group by group; groups[m] = [begin, end).
+struct Groups {
+    std::vector<int> order;
+    int begin[3] = {0, 0, 0}, end[3] = {0, 0, 0};
+    int max_p[3] = {0, 0, 0}, max_tiles[3] = {1, 1, 1};
+};
+
+Groups group_by_mode(img_ctx *const *ctxs, int n) {
+    Groups g;
+    for (int m = 0; m < 3; ++m) {
+        g.begin[m] = (int)g.order.size();
+        for (int j = 0; j < n; ++j) {
+            if (mode_of(ctxs[j]) != m) continue;
+            g.order.push_back(j);
+            g.max_p[m] = std::max(g.max_p[m], ctxs[j]->prm.p);
+            g.max_tiles[m] = std::max(g.max_tiles[m], (ctxs[j]->hj.Q + img::kTile - 1) / img::kTile);
+        }
+        g.end[m] = (int)g.order.size();
+    }
+    return g;
+}
+
+img_status check_batch(img_ctx *const *ctxs, int n) {
     if (!ctxs || n <= 0) return IMG_EINVAL;
     for (int j = 0; j < n; ++j) {
         if (!ctxs[j] || !ctxs[j]->has_cov) return IMG_EINVAL;
         if (ctxs[j]->device != ctxs[0]->device) return IMG_EINVAL;
     }
+    return IMG_OK;
+}
+
+// Factor + bounds of the listed jobs (device pointer array already in
+// g_ws.jobs in group order), one launch per kernel and group.
+img_status launch_prepare(const Groups &g, cudaStream_t s, int *status_out) {
+    for (int m = 0; m < 3; ++m) {
+        const int nb = g.end[m] - g.begin[m];
+        if (!nb) continue;
+        JobDev *const *jp = g_ws.jobs + g.begin[m];
+        CK(img::launch_factor(jp, nb, s));
+        CK(img::launch_bounds(jp, nb, g.max_tiles[m], g.max_p[m], m, s));
+        CK(img::launch_finalize(jp, nb, s, status_out ? status_out + g.begin[m] : nullptr));
+    }
+    return IMG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+img_status img_prepare_batch(img_ctx *const *ctxs, int n) {
+    img_status st = check_batch(ctxs, n);
+    if (st != IMG_OK) return st;
     std::lock_guard<std::mutex> lock(g_ws.mu);
-    img_status st = ws_reserve(n, ctxs[0]->device);
+    st = ws_reserve(n, ctxs[0]->device);
     if (st != IMG_OK) return st;
     cudaStream_t s = ctxs[0]->stream;
     for (int j = 0; j < n; ++j)
         if (ctxs[j]->stream != s) CK(cudaStreamSynchronize(ctxs[j]->stream));
+    const Groups g = group_by_mode(ctxs, n);
     std::vector<JobDev *> ptrs(n);
-    int max_p = 0, max_tiles = 1;
-    for (int j = 0; j < n; ++j) {
-        ptrs[j] = ctxs[j]->dj;
-        max_p = std::max(max_p, ctxs[j]->prm.p);
-        max_tiles = std::max(max_tiles, (ctxs[j]->hj.Q + img::kTile - 1) / img::kTile);
-    }
+    for (int q = 0; q < n; ++q) ptrs[q] = ctxs[g.order[q]]->dj;
     CK(cudaMemcpyAsync(g_ws.jobs, ptrs.data(), n * sizeof(JobDev *), cudaMemcpyHostToDevice, s));
-    CK(img::launch_factor(g_ws.jobs, n, s));
-    CK(img::launch_bounds(g_ws.jobs, n, max_tiles, max_p, s));
-    CK(img::launch_finalize(g_ws.jobs, n, s, g_ws.status));
+    st = launch_prepare(g, s, g_ws.status);
+    if (st != IMG_OK) return st;
     std::vector<int> flags(n);
     CK(cudaMemcpyAsync(flags.data(), g_ws.status, n * sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     img_status first = IMG_OK;
-    for (int j = 0; j < n; ++j) {
-        ctxs[j]->prepared = true;
-        ctxs[j]->prep_status = flags[j] == 0 ? IMG_OK : IMG_ENOTPD;
-        if (first == IMG_OK && flags[j] != 0) first = IMG_ENOTPD;
+    for (int q = 0; q < n; ++q) {
+        img_ctx *c = ctxs[g.order[q]];
+        c->prepared = true;
+        c->prep_status = flags[q] == 0 ? IMG_OK : IMG_ENOTPD;
     }
+    for (int j = 0; j < n; ++j)
+        if (first == IMG_OK && ctxs[j]->prep_status != IMG_OK) first = (img_status)ctxs[j]->prep_status;
     return first;
 }
 
 img_status img_solve_batch(img_ctx *const *ctxs, int n, double *const *sigma, img_solve_info *infos,
                            int on_device) {
-    if (!ctxs || n <= 0 || !sigma) return IMG_EINVAL;
-    for (int j = 0; j < n; ++j) {
-        if (!ctxs[j] || !sigma[j] || !ctxs[j]->has_cov) return IMG_EINVAL;
-        if (ctxs[j]->device != ctxs[0]->device) return IMG_EINVAL;
-    }
+    img_status st = check_batch(ctxs, n);
+    if (st != IMG_OK) return st;
+    if (!sigma) return IMG_EINVAL;
+    for (int j = 0; j < n; ++j)
+        if (!sigma[j]) return IMG_EINVAL;
     std::lock_guard<std::mutex> lock(g_ws.mu);
-    img_status st = ws_reserve(n, ctxs[0]->device);
+    st = ws_reserve(n, ctxs[0]->device);
     if (st != IMG_OK) return st;
     cudaStream_t s = ctxs[0]->stream;
-    // make every context's earlier work visible on the batch stream
     for (int j = 0; j < n; ++j)
         if (ctxs[j]->stream != s) CK(cudaStreamSynchronize(ctxs[j]->stream));
+    const Groups g = group_by_mode(ctxs, n);
     std::vector<JobDev *> ptrs(n);
-    std::vector<JobDev *> prep;
-    int max_p = 0, max_tiles = 1;
-    for (int j = 0; j < n; ++j) {
-        ptrs[j] = ctxs[j]->dj;
-        max_p = std::max(max_p, ctxs[j]->prm.p);
-        if (!ctxs[j]->prepared) {
-            prep.push_back(ctxs[j]->dj);
-            max_tiles = std::max(max_tiles, (ctxs[j]->hj.Q + img::kTile - 1) / img::kTile);
-        }
-    }
-    if (!prep.empty()) {
-        int np = (int)prep.size();
-        CK(cudaMemcpyAsync(g_ws.jobs, prep.data(), np * sizeof(JobDev *), cudaMemcpyHostToDevice, s));
-        CK(img::launch_factor(g_ws.jobs, np, s));
-        CK(img::launch_bounds(g_ws.jobs, np, max_tiles, max_p, s));
-        CK(img::launch_finalize(g_ws.jobs, np, s, nullptr));
+    std::vector<double *> outs(n);
+    bool need_prep = false;
+    for (int q = 0; q < n; ++q) {
+        ptrs[q] = ctxs[g.order[q]]->dj;
+        outs[q] = sigma[g.order[q]];
+        need_prep |= !ctxs[g.order[q]]->prepared;
     }
     CK(cudaMemcpyAsync(g_ws.jobs, ptrs.data(), n * sizeof(JobDev *), cudaMemcpyHostToDevice, s));
+    if (need_prep) {
+        // prepared jobs are simply recomputed: same inputs, same results
+        st = launch_prepare(g, s, nullptr);
+        if (st != IMG_OK) return st;
+    }
     if (on_device)
-        CK(cudaMemcpyAsync(g_ws.sig, sigma, n * sizeof(double *), cudaMemcpyHostToDevice, s));
-    CK(img::launch_solve(g_ws.jobs, n, max_p, g_ws.infos, on_device ? g_ws.sig : nullptr, s));
+        CK(cudaMemcpyAsync(g_ws.sig, outs.data(), n * sizeof(double *), cudaMemcpyHostToDevice, s));
+    for (int m = 0; m < 3; ++m) {
+        const int nb = g.end[m] - g.begin[m];
+        if (!nb) continue;
+        CK(img::launch_solve(g_ws.jobs + g.begin[m], nb, g.max_p[m], m, g_ws.infos + g.begin[m],
+                             on_device ? g_ws.sig + g.begin[m] : nullptr, s));
+    }
     std::vector<DevInfo> d(n);
     CK(cudaMemcpyAsync(d.data(), g_ws.infos, n * sizeof(DevInfo), cudaMemcpyDeviceToHost, s));
     if (!on_device)
@@ -522,12 +604,14 @@ img_status img_solve_batch(img_ctx *const *ctxs, int n, double *const *sigma, im
                                cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     img_status first = IMG_OK;
+    std::vector<DevInfo> byjob(n);
+    for (int q = 0; q < n; ++q) byjob[g.order[q]] = d[q];
     for (int j = 0; j < n; ++j) {
         ctxs[j]->prepared = true;
-        ctxs[j]->prep_status = d[j].status == IMG_ENOTPD ? IMG_ENOTPD : IMG_OK;
+        ctxs[j]->prep_status = byjob[j].status == IMG_ENOTPD ? IMG_ENOTPD : IMG_OK;
         ctxs[j]->solved = true;
-        if (infos) fill_info(&infos[j], d[j]);
-        if (first == IMG_OK && d[j].status != IMG_OK) first = (img_status)d[j].status;
+        if (infos) fill_info(&infos[j], byjob[j]);
+        if (first == IMG_OK && byjob[j].status != IMG_OK) first = (img_status)byjob[j].status;
     }
     return first;
 }

@@ -18,6 +18,9 @@ struct DevInfo {
     int converged;
     double lambda_min;
     double op_flops;
+    double cyc_total;
+    double cyc_gradient;
+    double cyc_lsqr;
 };
 
 // Everything one imaging job keeps on the device.  All pointers are device
@@ -27,7 +30,7 @@ struct JobDev {
     int p, n_l, n_m, Q;
     int cost, bound, bias_c, inflate;
     int lsqr_maxit, max_outer, cap, precision;
-    double alpha, kappa, eps_floor, lam, lsqr_atol, lsqr_btol;
+    double alpha, kappa, eps_floor, lam, lsqr_atol, lsqr_btol, feas_tol;
     long long N;
     // geometry (copied from the host)
     const double *ant;     // p*3 row-major
@@ -62,6 +65,11 @@ struct JobDev {
     int *fpos;             // cap, positions in supp of the free pixels
     float *v, *w, *xs;     // cap, LSQR vectors indexed by F position
     float2 *W0, *W1, *W2;  // p*p scratch matrices
+    // decision log (Table I order): kind << 24 | pixel, and lambda or mu
+    int *ev;
+    float *evv;
+    int ev_cap;
+    int *ev_count;
     // status and report
     DevInfo *info;
     int *flags;            // [0]: factor status, [1]: bounds valid
@@ -71,21 +79,23 @@ struct JobDev {
 // `jobs` is a device array of n job pointers.
 cudaError_t launch_tables(JobDev *const *jobs, int n, cudaStream_t st);
 cudaError_t launch_factor(JobDev *const *jobs, int n, cudaStream_t st);
-cudaError_t launch_bounds(JobDev *const *jobs, int n, int max_tiles, int max_p,
+cudaError_t launch_bounds(JobDev *const *jobs, int n, int max_tiles, int max_p, int mode,
                           cudaStream_t st);
 cudaError_t launch_finalize(JobDev *const *jobs, int n, cudaStream_t st, int *batch_status);
-cudaError_t launch_solve(JobDev *const *jobs, int n, int max_p, DevInfo *batch_info,
+// mode: 0 CUDA-core FP32 operators, 1 tensor cores FP16x3, 2 tensor cores BF16x3
+cudaError_t launch_solve(JobDev *const *jobs, int n, int max_p, int mode, DevInfo *batch_info,
                          double *const *sigma_out, cudaStream_t st);
 cudaError_t launch_psi(const JobDev *job_dev, const float *wx, float2 *part, int nparts, int Q,
                        int p, double2 *Kout, cudaStream_t st);
 cudaError_t launch_psi_adj(const JobDev *job_dev, const float2 *U, double *out, int Q, int p,
-                           cudaStream_t st);
+                           int mode, cudaStream_t st);
 cudaError_t launch_z2c(const double2 *src, float2 *dst, int n, cudaStream_t st);
 cudaError_t launch_c2z(const float2 *src, double2 *dst, int n, cudaStream_t st);
 cudaError_t launch_d2f(const double *src, float *dst, int n, cudaStream_t st);
 cudaError_t launch_to_double(const float *src, double *dst, int n, cudaStream_t st);
 
-size_t solve_smem_bytes(int p);
+size_t solve_smem_bytes(int p, int mode);
+constexpr int kMaxTcP = 64;   // tensor-core operators need 2p x 2p tiles in shared memory
 size_t bounds_smem_bytes(int p);
 
 }  // namespace img

@@ -8,6 +8,7 @@
 //   k_solve     persistent active-set + LSQR driver, one CTA per job
 //               (Table I, Sec. V-A, Sec. V-B)
 #include "cta_ops.cuh"
+#include "tc_ops.cuh"
 #include "../../include/img.h"
 
 namespace img {
@@ -142,6 +143,93 @@ __global__ void k_bounds(JobDev *const *jobs) {
     }
 }
 
+// Tensor-core form of k_bounds: pass 1 with B = R_hat (dirty image), pass 2
+// with B = R_hat^-1 (MVDR denominators), over 128-pixel tiles.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1) k_bounds_tc(JobDev *const *jobs) {
+    const JobDev &J = *jobs[blockIdx.y];
+    if (J.flags[0] != 0) return;
+    constexpr bool BF = MODE == 2;
+    extern __shared__ float4 smem4[];
+    unsigned char *dyn = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem4) + 1023) & ~uintptr_t(1023));
+    __shared__ uint64_t bar;
+    __shared__ uint32_t slot;
+    __shared__ double dbuf[kThreads / 32];
+    __shared__ float red[2 * kTcM];
+    TcWork T{};
+    tc_carve(T, dyn, J.p);
+    T.bar = &bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    if (threadIdx.x < 32) tmem_alloc(&slot, tc_tmem_cols(J.p));
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    T.tmem = slot;
+    const float sX = steer_scale(J.p);
+    const uint32_t idesc = idesc_f16(2 * T.Kp, BF ? 1 : 0);
+    const int ntiles = (J.Q + kTcM - 1) / kTcM;
+    for (int pass = 0; pass < 2; ++pass) {
+        const float sB = tc_build_B<BF>(pass == 0 ? J.R32 : J.Ri32, J.p, T, dbuf);
+        const float inv = 1.f / (sX * sB);
+        float *dst = pass == 0 ? J.dirty : J.h;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const int pix0 = t * kTcM;
+            const int np = min(kTcM, J.Q - pix0);
+            tc_gen_X_steer<BF>(J, T, pix0, np, sX);
+            tc_mma_tile(T, idesc);
+            tc_epilogue_steer(J, T, pix0, np, red);
+            if (threadIdx.x < np) dst[pix0 + threadIdx.x] = red[threadIdx.x] * inv;
+            __syncthreads();
+        }
+    }
+    if (T.timeouts && threadIdx.x == 0) J.flags[2] = IMG_ETIMEOUT;
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) tmem_dealloc(T.tmem, tc_tmem_cols(J.p));
+}
+
+// Tensor-core Psi^H vect(U) over all pixels of one job.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1) k_psi_adj_tc(const JobDev *Jp, const float2 *U,
+                                                           double *out) {
+    const JobDev &J = *Jp;
+    constexpr bool BF = MODE == 2;
+    extern __shared__ float4 smem4[];
+    unsigned char *dyn = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem4) + 1023) & ~uintptr_t(1023));
+    __shared__ uint64_t bar;
+    __shared__ uint32_t slot;
+    __shared__ double dbuf[kThreads / 32];
+    __shared__ float red[2 * kTcM];
+    TcWork T{};
+    tc_carve(T, dyn, J.p);
+    T.bar = &bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    if (threadIdx.x < 32) tmem_alloc(&slot, tc_tmem_cols(J.p));
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    T.tmem = slot;
+    const float sX = steer_scale(J.p);
+    const uint32_t idesc = idesc_f16(2 * T.Kp, BF ? 1 : 0);
+    const float sB = tc_build_B<BF>(U, J.p, T, dbuf);
+    const float inv = 1.f / (sX * sB);
+    const int ntiles = (J.Q + kTcM - 1) / kTcM;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int pix0 = t * kTcM;
+        const int np = min(kTcM, J.Q - pix0);
+        tc_gen_X_steer<BF>(J, T, pix0, np, sX);
+        tc_mma_tile(T, idesc);
+        tc_epilogue_steer(J, T, pix0, np, red);
+        if (threadIdx.x < np) out[pix0 + threadIdx.x] = red[threadIdx.x] * inv;
+        __syncthreads();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) tmem_dealloc(T.tmem, tc_tmem_cols(J.p));
+}
+
 // Bounds, preconditioner and thresholds (one CTA per job):
 //   C = N/(N-p) or 1; mvdr = C/h; D = h^2/C; std_MF = dirty/sqrt(N);
 //   std_MVDR = mvdr/sqrt(N-p-1); gamma = chosen image, optionally inflated;
@@ -216,17 +304,67 @@ __device__ void cache_vector(const JobDev &J, int i, int slot) {
 }
 
 // Adjoint over a list of cached vectors: t_j = Re(c_j^H U c_j), handed to
-// epi(j, t_j) on threads < kTile.
-template <class Epi>
+// epi(j, t_j) on threads < tile size.  MODE 0: CUDA cores (FP32); 1/2:
+// tensor cores with split FP16 / BF16 operands.
+template <int MODE, class Epi>
 __device__ void adjoint_list(const JobDev &J, const float2 *U, const int *pos, int n, float2 *A,
-                             float *red, Epi epi) {
-    for (int j0 = 0; j0 < n; j0 += kTile) {
-        const int np = min(kTile, n - j0);
-        fill_cache_adj(J, pos, j0, np, A);
-        __syncthreads();
-        adj_chunk(U, J.p, A, red);
-        if (threadIdx.x < np) epi(j0 + threadIdx.x, red[threadIdx.x]);
-        __syncthreads();
+                             TcWork &T, float *red, double *dbuf, Epi epi) {
+    if constexpr (MODE == 0) {
+        for (int j0 = 0; j0 < n; j0 += kTile) {
+            const int np = min(kTile, n - j0);
+            fill_cache_adj(J, pos, j0, np, A);
+            __syncthreads();
+            adj_chunk(U, J.p, A, red);
+            if (threadIdx.x < np) epi(j0 + threadIdx.x, red[threadIdx.x]);
+            __syncthreads();
+        }
+    } else {
+        constexpr bool BF = MODE == 2;
+        const float sB = tc_build_B<BF>(U, J.p, T, dbuf);
+        const uint32_t idesc = idesc_f16(2 * T.Kp, BF ? 1 : 0);
+        for (int j0 = 0; j0 < n; j0 += kTcM) {
+            const int np = min(kTcM, n - j0);
+            const float sX = tc_gen_X_cache<BF>(J, T, pos, j0, np, dbuf);
+            tc_mma_tile(T, idesc);
+            tc_epilogue_cache(J, T, pos, j0, np, red);
+            const float inv = 1.f / (sX * sB);
+            if (threadIdx.x < np) epi(j0 + threadIdx.x, red[threadIdx.x] * inv);
+            __syncthreads();
+        }
+    }
+}
+
+// Full-image adjoint with generated steering vectors: epi(i, Re(a_i^H U a_i))
+// for every pixel, on one thread per pixel.
+template <int MODE, class Epi>
+__device__ void adjoint_full(const JobDev &J, const float2 *U, float2 *A, TcWork &T, float *red,
+                             double *dbuf, Epi epi) {
+    const int Q = J.Q;
+    if constexpr (MODE == 0) {
+        const int ntiles = (Q + kTile - 1) / kTile;
+        for (int t = 0; t < ntiles; ++t) {
+            const int pix0 = t * kTile;
+            const int np = min(kTile, Q - pix0);
+            fill_steer_adj(J, pix0, np, A);
+            __syncthreads();
+            adj_chunk(U, J.p, A, red);
+            if (threadIdx.x < np) epi(pix0 + threadIdx.x, red[threadIdx.x]);
+            __syncthreads();
+        }
+    } else {
+        constexpr bool BF = MODE == 2;
+        const float sB = tc_build_B<BF>(U, J.p, T, dbuf);
+        const float sX = steer_scale(J.p);
+        const float inv = 1.f / (sX * sB);
+        const uint32_t idesc = idesc_f16(2 * T.Kp, BF ? 1 : 0);
+        for (int pix0 = 0; pix0 < Q; pix0 += kTcM) {
+            const int np = min(kTcM, Q - pix0);
+            tc_gen_X_steer<BF>(J, T, pix0, np, sX);
+            tc_mma_tile(T, idesc);
+            tc_epilogue_steer(J, T, pix0, np, red);
+            if (threadIdx.x < np) epi(pix0 + threadIdx.x, red[threadIdx.x] * inv);
+            __syncthreads();
+        }
     }
 }
 
@@ -235,7 +373,8 @@ __device__ void adjoint_list(const JobDev &J, const float2 *U, const int *pos, i
 // b is in J.W0 on entry.  The bidiagonalisation follows eq. initbeta ..
 // eq. lanczos; rotations and stopping tests as in the FP64 oracle, scalars
 // in FP64.  Returns the iteration count; the solution is in J.xs[0..f).
-__device__ int lsqr_cta(const JobDev &J, int f, float2 *A, SolveShared &S) {
+template <int MODE>
+__device__ int lsqr_cta(const JobDev &J, int f, float2 *A, TcWork &T, SolveShared &S) {
     const int p = J.p, pp = p * p;
     float2 *u = J.W0;
     double acc = 0.0;
@@ -250,7 +389,7 @@ __device__ int lsqr_cta(const JobDev &J, int f, float2 *A, SolveShared &S) {
     }
     __syncthreads();
     const int *fpos = J.fpos;
-    adjoint_list(J, u, fpos, f, A, S.red, [&](int j, float t) {
+    adjoint_list<MODE>(J, u, fpos, f, A, T, S.red, S.dbuf, [&](int j, float t) {
         J.v[j] = J.scale[J.supp[fpos[j]]] * t;
     });
     acc = 0.0;
@@ -291,7 +430,7 @@ __device__ int lsqr_cta(const JobDev &J, int f, float2 *A, SolveShared &S) {
         anorm2 += alpha * alpha + beta * beta;
         // v <- M^H u - beta v
         const float fb = (float)beta;
-        adjoint_list(J, u, fpos, f, A, S.red, [&](int j, float t) {
+        adjoint_list<MODE>(J, u, fpos, f, A, T, S.red, S.dbuf, [&](int j, float t) {
             J.v[j] = J.scale[J.supp[fpos[j]]] * t - fb * J.v[j];
         });
         acc = 0.0;
@@ -349,13 +488,20 @@ __device__ void supp_remove(const JobDev &J, int i, int &ns) {
     __syncthreads();
 }
 
-// Persistent active-set driver (Table I), one CTA per job.
+// Persistent active-set driver (Table I), one CTA per job.  MODE selects the
+// adjoint's arithmetic (0 CUDA cores FP32, 1 tensor cores FP16x3, 2 BF16x3).
+template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
 k_solve(JobDev *const *jobs, DevInfo *batch_info, double *const *sigma_out) {
     const JobDev &J = *jobs[blockIdx.x];
     extern __shared__ float4 smem4[];
-    float2 *A = reinterpret_cast<float2 *>(smem4);
+    // one 1024-aligned region serves the CUDA-core chunk or the tensor tiles
+    unsigned char *dyn = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem4) + 1023) & ~uintptr_t(1023));
+    float2 *A = reinterpret_cast<float2 *>(dyn);
     __shared__ SolveShared S;
+    __shared__ uint64_t tc_bar;
+    __shared__ uint32_t tc_slot;
     DevInfo info{};
     info.status = IMG_OK;
     if (J.flags[0] != 0 || J.flags[1] != 1) {
@@ -368,6 +514,17 @@ k_solve(JobDev *const *jobs, DevInfo *batch_info, double *const *sigma_out) {
     }
     const int p = J.p, Q = J.Q;
     const bool pwls = J.cost == IMG_COST_PWLS;
+    TcWork T{};
+    if constexpr (MODE != 0) {
+        tc_carve(T, dyn, p);
+        T.bar = &tc_bar;
+        if (threadIdx.x == 0) mbar_init(&tc_bar, 1);
+        if (threadIdx.x < 32) tmem_alloc(&tc_slot, tc_tmem_cols(p));
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        T.tmem = tc_slot;
+    }
     for (int i = threadIdx.x; i < Q; i += blockDim.x) {
         J.x[i] = 0.0;
         J.set[i] = IMG_SET_L;
@@ -375,6 +532,15 @@ k_solve(JobDev *const *jobs, DevInfo *batch_info, double *const *sigma_out) {
         J.grad[i] = 0.f;
     }
     __syncthreads();
+    const long long t_start = clock64();
+    int nev = 0;          // decisions so far
+    auto log_event = [&](int kind, int pixel, float val) {
+        if (threadIdx.x == 0 && nev < J.ev_cap) {
+            J.ev[nev] = (kind << 24) | pixel;
+            J.evv[nev] = val;
+        }
+        ++nev;
+    };
     int ns = 0;           // support size |F u U|
     bool flag = true;     // Freegradient-isnotzero
     int imin = -1;
@@ -400,19 +566,26 @@ k_solve(JobDev *const *jobs, DevInfo *batch_info, double *const *sigma_out) {
                 __syncthreads();
                 forward_list(J, J.fpos + f, wt, nu, false, pwls ? nullptr : J.R32, pwls, J.W0, A, S.wsm);
                 info.op_flops += flops_fwd(p, nu);
-                const int its = lsqr_cta(J, f, A, S);
+                const long long t0 = clock64();
+                const int its = lsqr_cta<MODE>(J, f, A, T, S);
+                info.cyc_lsqr += (double)(clock64() - t0);
                 info.lsqr_iters += its;
                 info.op_flops += (its + 1) * (flops_fwd(p, f) + flops_adj(p, f));
+                // feasibility with the relative tolerance tau, non-strict
                 int bad = 0;
+                const double tau = J.feas_tol;
                 for (int j = threadIdx.x; j < f; j += blockDim.x) {
                     const double z = J.xs[j];
-                    const int i = J.supp[J.fpos[j]];
-                    if (!(z >= 0.0 && z <= J.upper[i])) bad = 1;
+                    const double u = J.upper[J.supp[J.fpos[j]]];
+                    if (!(z >= -tau * u && z <= (1.0 + tau) * u)) bad = 1;
                 }
                 feasible = __syncthreads_or(bad) == 0;
             }
             if (feasible) {
-                for (int j = threadIdx.x; j < f; j += blockDim.x) J.x[J.supp[J.fpos[j]]] = (double)J.xs[j];
+                for (int j = threadIdx.x; j < f; j += blockDim.x) {
+                    const int i = J.supp[J.fpos[j]];
+                    J.x[i] = fmin(fmax((double)J.xs[j], 0.0), J.upper[i]);
+                }
                 flag = false;
                 __syncthreads();
                 // gradient: E = B0 - sum_S s_i x_i c_i c_i^H, U_g = T^H E T
@@ -429,32 +602,24 @@ k_solve(JobDev *const *jobs, DevInfo *batch_info, double *const *sigma_out) {
                     cgemm_pp(p, J.Li32, true, J.W2, J.W0);
                     Ug = J.W0;
                 }
+                const long long tg = clock64();
                 double best = INFINITY;
                 int bidx = 0x7fffffff;
-                const int ntiles = (Q + kTile - 1) / kTile;
-                for (int t = 0; t < ntiles; ++t) {
-                    const int pix0 = t * kTile;
-                    const int np = min(kTile, Q - pix0);
-                    fill_steer_adj(J, pix0, np, A);
-                    __syncthreads();
-                    adj_chunk(Ug, p, A, S.red);
-                    if (threadIdx.x < np) {
-                        const int i = pix0 + threadIdx.x;
-                        const float g = -J.scale[i] * S.red[threadIdx.x];
-                        J.grad[i] = g;
-                        const unsigned char st = J.set[i];
-                        if (st != IMG_SET_F) {
-                            const double lam = st == IMG_SET_U ? -(double)g : (double)g;
-                            if (lam < -(double)J.eps[i] && (lam < best || (lam == best && i < bidx))) {
-                                best = lam;
-                                bidx = i;
-                            }
+                adjoint_full<MODE>(J, Ug, A, T, S.red, S.dbuf, [&](int i, float val) {
+                    const float g = -J.scale[i] * val;
+                    J.grad[i] = g;
+                    const unsigned char st = J.set[i];
+                    if (st != IMG_SET_F) {
+                        const double lam = st == IMG_SET_U ? -(double)g : (double)g;
+                        if (lam < -(double)J.eps[i] && (lam < best || (lam == best && i < bidx))) {
+                            best = lam;
+                            bidx = i;
                         }
                     }
-                    __syncthreads();
-                }
+                });
                 info.op_flops += flops_adj(p, Q);
                 block_argmin(best, bidx, S.vbuf, S.ibuf);
+                info.cyc_gradient += (double)(clock64() - tg);
                 lam_min = best;
                 if (bidx == 0x7fffffff) {
                     converged = true;
@@ -492,6 +657,7 @@ k_solve(JobDev *const *jobs, DevInfo *batch_info, double *const *sigma_out) {
                     J.set[ic] = up ? IMG_SET_U : IMG_SET_L;
                     J.x[ic] = up ? J.upper[ic] : 0.0;
                 }
+                log_event(up ? 2 : 1, ic, (float)mu);
                 __syncthreads();
                 if (!up) supp_remove(J, ic, ns);
                 flag = true;
@@ -512,11 +678,18 @@ k_solve(JobDev *const *jobs, DevInfo *batch_info, double *const *sigma_out) {
                 ++ns;
             }
             if (threadIdx.x == 0) J.set[i] = IMG_SET_F;
+            log_event(0, i, (float)lam_min);
             __syncthreads();
             flag = true;
         }
     }
     if (!converged && info.status == IMG_OK) info.status = IMG_ENOTCONV;
+    if constexpr (MODE != 0) {
+        if (T.timeouts && info.status == IMG_OK) info.status = IMG_ETIMEOUT;
+        tc_fence_before();
+        __syncthreads();
+        if (threadIdx.x < 32) tmem_dealloc(T.tmem, tc_tmem_cols(p));
+    }
     double *out = sigma_out ? sigma_out[blockIdx.x] : nullptr;
     int nf = 0, nu = 0;
     for (int i = threadIdx.x; i < Q; i += blockDim.x) {
@@ -534,6 +707,8 @@ k_solve(JobDev *const *jobs, DevInfo *batch_info, double *const *sigma_out) {
         info.n_upper = (int)tu;
         info.converged = converged ? 1 : 0;
         info.lambda_min = lam_min;
+        info.cyc_total = (double)(clock64() - t_start);
+        *J.ev_count = nev;
         *J.info = info;
         if (batch_info) batch_info[blockIdx.x] = info;
     }
@@ -656,7 +831,11 @@ __global__ void k_d2f(const double *src, float *dst, int n) {
 }
 
 // ---------------------------------------------------------------- launchers
-size_t solve_smem_bytes(int p) { return (size_t)p * kTile * sizeof(float2); }
+size_t solve_smem_bytes(int p, int mode) {
+    size_t b = (size_t)p * kTile * sizeof(float2);
+    if (mode != 0) b = b > tc_smem_bytes(p) ? b : tc_smem_bytes(p);
+    return b + 1024;
+}
 size_t bounds_smem_bytes(int p) {
     return (size_t)p * kTile * sizeof(float2) + (kTile + 16 * kTile) * sizeof(float);
 }
@@ -682,7 +861,20 @@ cudaError_t launch_factor(JobDev *const *jobs, int n, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_bounds(JobDev *const *jobs, int n, int max_tiles, int max_p, cudaStream_t st) {
+template <int MODE>
+static cudaError_t launch_bounds_tc_t(JobDev *const *jobs, int n, int max_tiles, int max_p, cudaStream_t st) {
+    const size_t sm = tc_smem_bytes(max_p) + 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_bounds_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int per_job = (num_sms() + n - 1) / n;
+    per_job = max(1, min(per_job, max_tiles));
+    k_bounds_tc<MODE><<<dim3(per_job, n), kThreads, sm, st>>>(jobs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bounds(JobDev *const *jobs, int n, int max_tiles, int max_p, int mode, cudaStream_t st) {
+    if (mode == 1) return launch_bounds_tc_t<1>(jobs, n, (max_tiles + 1) / 2, max_p, st);
+    if (mode == 2) return launch_bounds_tc_t<2>(jobs, n, (max_tiles + 1) / 2, max_p, st);
     const size_t sm = bounds_smem_bytes(max_p);
     cudaError_t e = cudaFuncSetAttribute(k_bounds, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -697,13 +889,21 @@ cudaError_t launch_finalize(JobDev *const *jobs, int n, cudaStream_t st, int *ba
     return cudaGetLastError();
 }
 
-cudaError_t launch_solve(JobDev *const *jobs, int n, int max_p, DevInfo *batch_info,
-                         double *const *sigma_out, cudaStream_t st) {
-    const size_t sm = solve_smem_bytes(max_p);
-    cudaError_t e = cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+template <int MODE>
+static cudaError_t launch_solve_t(JobDev *const *jobs, int n, size_t sm, DevInfo *batch_info,
+                                  double *const *sigma_out, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(k_solve<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_solve<<<n, kThreads, sm, st>>>(jobs, batch_info, sigma_out);
+    k_solve<MODE><<<n, kThreads, sm, st>>>(jobs, batch_info, sigma_out);
     return cudaGetLastError();
+}
+
+cudaError_t launch_solve(JobDev *const *jobs, int n, int max_p, int mode, DevInfo *batch_info,
+                         double *const *sigma_out, cudaStream_t st) {
+    const size_t sm = solve_smem_bytes(max_p, mode);
+    if (mode == 1) return launch_solve_t<1>(jobs, n, sm, batch_info, sigma_out, st);
+    if (mode == 2) return launch_solve_t<2>(jobs, n, sm, batch_info, sigma_out, st);
+    return launch_solve_t<0>(jobs, n, sm, batch_info, sigma_out, st);
 }
 
 // Psi x over all pixels: nparts CTAs write partial p x p sums into `part`
@@ -723,8 +923,21 @@ cudaError_t launch_psi(const JobDev *job_dev, const float *wx, float2 *part, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_psi_adj(const JobDev *job_dev, const float2 *U, double *out, int Q, int p,
+template <int MODE>
+static cudaError_t launch_psi_adj_tc_t(const JobDev *job_dev, const float2 *U, double *out, int Q, int p,
+                                       cudaStream_t st) {
+    const size_t sm = tc_smem_bytes(p) + 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_psi_adj_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const int ntiles = (Q + kTcM - 1) / kTcM;
+    k_psi_adj_tc<MODE><<<min(ntiles, num_sms()), kThreads, sm, st>>>(job_dev, U, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_psi_adj(const JobDev *job_dev, const float2 *U, double *out, int Q, int p, int mode,
                            cudaStream_t st) {
+    if (mode == 1) return launch_psi_adj_tc_t<1>(job_dev, U, out, Q, p, st);
+    if (mode == 2) return launch_psi_adj_tc_t<2>(job_dev, U, out, Q, p, st);
     const size_t sm = bounds_smem_bytes(p);
     cudaError_t e = cudaFuncSetAttribute(k_psi_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;

@@ -22,9 +22,9 @@ RECORDS = {
     # 128x128 grid, p = 64 log-spiral, 20 points + Gaussian blob, N = 1e4,
     # PWLS with the MVDR bound, kappa = 6 (the bench workload's image)
     "mid_pwls": dict(maker=lambda: synth.mid(), prm=O.Params(cost=O.COST_PWLS, kappa=6.0,
-                                                                eps_floor=1e-6)),
+                                                                eps_floor=1e-6, feas_tol=1e-5)),
     "mid_ls": dict(maker=lambda: synth.mid(), prm=O.Params(cost=O.COST_LS, kappa=6.0,
-                                                            eps_floor=1e-6)),
+                                                            eps_floor=1e-6, feas_tol=1e-5)),
 }
 
 
@@ -38,7 +38,7 @@ def make(name: str) -> str:
     out = os.path.join(HERE, f"{name}.npz")
     np.savez_compressed(
         out, ant_xyz=job.ant_xyz, l=job.l, m=job.m, lam=job.lam, R=job.R, N=job.N,
-        cost=prm.cost, kappa=prm.kappa, eps_floor=prm.eps_floor,
+        cost=prm.cost, kappa=prm.kappa, eps_floor=prm.eps_floor, feas_tol=prm.feas_tol,
         dirty=res.bounds.dirty, mvdr=res.bounds.mvdr, gamma=res.bounds.gamma,
         sigma=res.solve.sigma, sets=res.solve.sets, outer=res.solve.outer,
         lsqr_iters=res.solve.lsqr_iters, converged=res.solve.converged,

@@ -12,6 +12,8 @@ pytestmark = pytest.mark.gpu
 
 OP_TOL = 1e-5
 IMG_TOL = 1e-4
+# operator tolerance per arithmetic: FP32 CUDA cores, FP16x3 and BF16x3 tensor cores
+PREC_TOL = {0: 1e-5, 1: 1e-5, 2: 1e-4}
 
 
 @pytest.fixture(scope="module")
@@ -32,27 +34,30 @@ def _oracle_ops(job):
 
 
 # ---------------------------------------------------------------- operators
-@pytest.mark.parametrize("shape", [(16, 32, 32), (7, 13, 11), (33, 9, 17), (64, 8, 8)])
-def test_dirty_and_mvdr_match_oracle(G, shape):
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("shape", [(16, 32, 32), (7, 13, 11), (33, 9, 17), (64, 8, 8), (64, 40, 41)])
+def test_dirty_and_mvdr_match_oracle(G, shape, prec):
     p, nl, nm = shape
     job = synth.custom(100 + p, p, nl, nm, 3, 4 * p + 50, radius=5.0, snr_db=0.0)
     A, Psi = _oracle_ops(job)
     prm = O.Params(bias_c=1)
     b = O.bounds(A, Psi, job.R, job.N, prm)
-    im = G.Imager.from_job(job, bias_c=1)
+    im = G.Imager.from_job(job, bias_c=1, precision=prec)
     d = im.dirty()
     mv = im.mvdr_bound()
-    assert _rel(d, b.dirty) <= OP_TOL
-    assert np.max(np.abs(d - b.dirty) / b.dirty) <= 10 * OP_TOL
-    assert _rel(mv, b.mvdr) <= OP_TOL
+    tol = PREC_TOL[prec]
+    assert _rel(d, b.dirty) <= tol
+    assert np.max(np.abs(d - b.dirty) / b.dirty) <= 10 * tol
+    assert _rel(mv, b.mvdr) <= tol
     assert np.all(mv / b.C <= d * (1 + 1e-5))      # Cauchy-Schwarz holds for C = 1
     im.close()
 
 
-def test_psi_pair_matches_explicit_khatri_rao(G):
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_psi_pair_matches_explicit_khatri_rao(G, prec):
     job = synth.custom(5, 9, 10, 7, 2, 400, radius=3.0)
     A, Psi = _oracle_ops(job)
-    im = G.Imager.from_job(job)
+    im = G.Imager.from_job(job, precision=prec)
     rng = np.random.default_rng(1)
     x = rng.random(job.Q)
     K = im.psi(x)
@@ -62,25 +67,26 @@ def test_psi_pair_matches_explicit_khatri_rao(G):
     U = X + X.conj().T
     y = im.psi_adj(U)
     refy = np.real(Psi.conj().T @ O.vect(U))
-    assert _rel(y, refy) <= OP_TOL
+    assert _rel(y, refy) <= PREC_TOL[prec]
     # adjoint identity on the GPU operators: <Psi x, U> = <x, Psi^H U>
     lhs = np.real(np.vdot(O.vect(K), O.vect(U)))
     rhs = float(x @ y)
-    assert abs(lhs - rhs) <= 1e-5 * np.linalg.norm(O.vect(K)) * np.linalg.norm(O.vect(U))
+    assert abs(lhs - rhs) <= PREC_TOL[prec] * np.linalg.norm(O.vect(K)) * np.linalg.norm(O.vect(U))
     im.close()
 
 
 # ---------------------------------------------------------------- solve
 def _oracle_image(job, cost, kappa, eps_floor):
-    prm = O.Params(cost=cost, kappa=kappa, eps_floor=eps_floor)
+    prm = O.Params(cost=cost, kappa=kappa, eps_floor=eps_floor, feas_tol=1e-5)
     return O.image_job(job, prm)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("cost", [0, 1])
-def test_tiny_solve_matches_oracle(G, cost):
+def test_tiny_solve_matches_oracle(G, cost, prec):
     job = synth.tiny()
     ref = _oracle_image(job, cost, 6.0, 1e-6)
-    im = G.Imager.from_job(job, cost=cost, kappa=6.0, eps_floor=1e-6)
+    im = G.Imager.from_job(job, cost=cost, kappa=6.0, eps_floor=1e-6, precision=prec)
     sigma, info = im.solve()
     assert info.converged == 1
     assert _rel(sigma, ref.solve.sigma) <= IMG_TOL
@@ -89,11 +95,12 @@ def test_tiny_solve_matches_oracle(G, cost):
     im.close()
 
 
+@pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("seed", [41, 42])
-def test_ragged_solve_matches_oracle(G, seed):
+def test_ragged_solve_matches_oracle(G, seed, prec):
     job = synth.custom(seed, 11, 19, 13, 4, 800, radius=4.0, snr_db=0.0)
     ref = _oracle_image(job, 1, 6.0, 1e-6)
-    im = G.Imager.from_job(job, kappa=6.0, eps_floor=1e-6)
+    im = G.Imager.from_job(job, kappa=6.0, eps_floor=1e-6, precision=prec)
     sigma, info = im.solve()
     assert info.converged == 1
     assert _rel(sigma, ref.solve.sigma) <= IMG_TOL
