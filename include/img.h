@@ -130,6 +130,8 @@ typedef struct {
     double cyc_total;    /* SM clock cycles of the solve                     */
     double cyc_gradient; /* ... of which in full-image gradients             */
     double cyc_lsqr;     /* ... of which in LSQR subproblems                 */
+    double cyc_lsqr_fwd; /* ... of which in LSQR's forward products M v      */
+    double cyc_lsqr_adj; /* ... of which in LSQR's adjoint products M^H u    */
 } img_solve_info;
 
 /* Fill *prm with defaults: PWLS, MVDR bound, C = 1, no inflation, kappa 6,

@@ -44,7 +44,8 @@ class SolveInfo(C.Structure):
                 ("n_free", C.c_int), ("n_upper", C.c_int), ("converged", C.c_int),
                 ("lambda_min", C.c_double), ("op_flops", C.c_double),
                 ("cyc_total", C.c_double), ("cyc_gradient", C.c_double),
-                ("cyc_lsqr", C.c_double)]
+                ("cyc_lsqr", C.c_double), ("cyc_lsqr_fwd", C.c_double),
+                ("cyc_lsqr_adj", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

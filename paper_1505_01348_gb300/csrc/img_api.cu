@@ -94,6 +94,7 @@ size_t carve(img_ctx *c, char *base) {
     J.slot = cv.take<int>(Q);
     J.supp = cv.take<int>(cap);
     J.cvec = cv.take<float2>((size_t)cap * p);
+    J.cmax = cv.take<float>(cap);
     J.fpos = cv.take<int>(cap);
     J.v = cv.take<float>(cap);
     J.w = cv.take<float>(cap);
@@ -206,6 +207,8 @@ void fill_info(img_solve_info *o, const DevInfo &d) {
     o->cyc_total = d.cyc_total;
     o->cyc_gradient = d.cyc_gradient;
     o->cyc_lsqr = d.cyc_lsqr;
+    o->cyc_lsqr_fwd = d.cyc_lsqr_fwd;
+    o->cyc_lsqr_adj = d.cyc_lsqr_adj;
 }
 
 }  // namespace
@@ -460,7 +463,7 @@ img_status img_psi(img_ctx *c, const double *x, double *Kout, int on_device) {
         CK(cudaMemcpyAsync(c->wx, f.data(), Q * sizeof(float), cudaMemcpyHostToDevice, c->stream));
         CK(cudaStreamSynchronize(c->stream));
     }
-    CK(img::launch_psi(c->dj, c->wx, c->part, c->nparts, Q, p, c->Z, c->stream));
+    CK(img::launch_psi(c->dj, c->wx, c->part, c->nparts, Q, p, mode_of(c), c->Z, c->stream));
     CK(cudaMemcpyAsync(Kout, c->Z, (size_t)p * p * sizeof(double2),
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
     return sync(c);

@@ -21,6 +21,8 @@ struct DevInfo {
     double cyc_total;
     double cyc_gradient;
     double cyc_lsqr;
+    double cyc_lsqr_fwd;
+    double cyc_lsqr_adj;
 };
 
 // Everything one imaging job keeps on the device.  All pointers are device
@@ -62,6 +64,7 @@ struct JobDev {
     // support S = F u U: pixel ids and cached (whitened) steering vectors
     int *supp;             // cap
     float2 *cvec;          // cap * p, c_i = T a_i (T = L^-1 for PWLS, I for LS)
+    float *cmax;           // cap, max over k of |Re c_i[k]|, |Im c_i[k]|
     int *fpos;             // cap, positions in supp of the free pixels
     float *v, *w, *xs;     // cap, LSQR vectors indexed by F position
     float2 *W0, *W1, *W2;  // p*p scratch matrices
@@ -86,7 +89,7 @@ cudaError_t launch_finalize(JobDev *const *jobs, int n, cudaStream_t st, int *ba
 cudaError_t launch_solve(JobDev *const *jobs, int n, int max_p, int mode, DevInfo *batch_info,
                          double *const *sigma_out, cudaStream_t st);
 cudaError_t launch_psi(const JobDev *job_dev, const float *wx, float2 *part, int nparts, int Q,
-                       int p, double2 *Kout, cudaStream_t st);
+                       int p, int mode, double2 *Kout, cudaStream_t st);
 cudaError_t launch_psi_adj(const JobDev *job_dev, const float2 *U, double *out, int Q, int p,
                            int mode, cudaStream_t st);
 cudaError_t launch_z2c(const double2 *src, float2 *dst, int n, cudaStream_t st);

@@ -153,40 +153,37 @@ __global__ void __launch_bounds__(kThreads, 1) k_bounds_tc(JobDev *const *jobs) 
     extern __shared__ float4 smem4[];
     unsigned char *dyn = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem4) + 1023) & ~uintptr_t(1023));
-    __shared__ uint64_t bar;
+    __shared__ uint64_t bars[2];
     __shared__ uint32_t slot;
     __shared__ double dbuf[kThreads / 32];
     __shared__ float red[2 * kTcM];
     TcWork T{};
     tc_carve(T, dyn, J.p);
-    T.bar = &bar;
-    if (threadIdx.x == 0) mbar_init(&bar, 1);
-    if (threadIdx.x < 32) tmem_alloc(&slot, tc_tmem_cols(J.p));
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    T.tmem = slot;
+    tc_setup(T, bars, &slot, J.p);
     const float sX = steer_scale(J.p);
     const uint32_t idesc = idesc_f16(2 * T.Kp, BF ? 1 : 0);
     const int ntiles = (J.Q + kTcM - 1) / kTcM;
+    const int mine = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     for (int pass = 0; pass < 2; ++pass) {
         const float sB = tc_build_B<BF>(pass == 0 ? J.R32 : J.Ri32, J.p, T, dbuf);
-        const float inv = 1.f / (sX * sB);
+        const float inv = 1.f / (sX * sX * sB);
         float *dst = pass == 0 ? J.dirty : J.h;
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-            const int pix0 = t * kTcM;
-            const int np = min(kTcM, J.Q - pix0);
-            tc_gen_X_steer<BF>(J, T, pix0, np, sX);
-            tc_mma_tile(T, idesc);
-            tc_epilogue_steer(J, T, pix0, np, red);
-            if (threadIdx.x < np) dst[pix0 + threadIdx.x] = red[threadIdx.x] * inv;
-            __syncthreads();
-        }
+        tc_run_tiles(
+            T, mine, idesc,
+            [&](int t, int b) {
+                const int pix0 = (blockIdx.x + t * gridDim.x) * kTcM;
+                tc_gen_X_steer<BF>(J, T, b, pix0, min(kTcM, J.Q - pix0), sX);
+            },
+            [&](int t, int b) {
+                const int pix0 = (blockIdx.x + t * gridDim.x) * kTcM;
+                const int np = min(kTcM, J.Q - pix0);
+                tc_epilogue<BF>(T, b, red);
+                if (threadIdx.x < np) dst[pix0 + threadIdx.x] = red[threadIdx.x] * inv;
+                __syncthreads();
+            });
     }
     if (T.timeouts && threadIdx.x == 0) J.flags[2] = IMG_ETIMEOUT;
-    tc_fence_before();
-    __syncthreads();
-    if (threadIdx.x < 32) tmem_dealloc(T.tmem, tc_tmem_cols(J.p));
+    tc_teardown(T, J.p);
 }
 
 // Tensor-core Psi^H vect(U) over all pixels of one job.
@@ -198,36 +195,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_psi_adj_tc(const JobDev *Jp, co
     extern __shared__ float4 smem4[];
     unsigned char *dyn = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem4) + 1023) & ~uintptr_t(1023));
-    __shared__ uint64_t bar;
+    __shared__ uint64_t bars[2];
     __shared__ uint32_t slot;
     __shared__ double dbuf[kThreads / 32];
     __shared__ float red[2 * kTcM];
     TcWork T{};
     tc_carve(T, dyn, J.p);
-    T.bar = &bar;
-    if (threadIdx.x == 0) mbar_init(&bar, 1);
-    if (threadIdx.x < 32) tmem_alloc(&slot, tc_tmem_cols(J.p));
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    T.tmem = slot;
+    tc_setup(T, bars, &slot, J.p);
     const float sX = steer_scale(J.p);
     const uint32_t idesc = idesc_f16(2 * T.Kp, BF ? 1 : 0);
     const float sB = tc_build_B<BF>(U, J.p, T, dbuf);
-    const float inv = 1.f / (sX * sB);
+    const float inv = 1.f / (sX * sX * sB);
     const int ntiles = (J.Q + kTcM - 1) / kTcM;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int pix0 = t * kTcM;
-        const int np = min(kTcM, J.Q - pix0);
-        tc_gen_X_steer<BF>(J, T, pix0, np, sX);
-        tc_mma_tile(T, idesc);
-        tc_epilogue_steer(J, T, pix0, np, red);
-        if (threadIdx.x < np) out[pix0 + threadIdx.x] = red[threadIdx.x] * inv;
-        __syncthreads();
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (threadIdx.x < 32) tmem_dealloc(T.tmem, tc_tmem_cols(J.p));
+    const int mine = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    tc_run_tiles(
+        T, mine, idesc,
+        [&](int t, int b) {
+            const int pix0 = (blockIdx.x + t * gridDim.x) * kTcM;
+            tc_gen_X_steer<BF>(J, T, b, pix0, min(kTcM, J.Q - pix0), sX);
+        },
+        [&](int t, int b) {
+            const int pix0 = (blockIdx.x + t * gridDim.x) * kTcM;
+            const int np = min(kTcM, J.Q - pix0);
+            tc_epilogue<BF>(T, b, red);
+            if (threadIdx.x < np) out[pix0 + threadIdx.x] = red[threadIdx.x] * inv;
+            __syncthreads();
+        });
+    tc_teardown(T, J.p);
 }
 
 // Bounds, preconditioner and thresholds (one CTA per job):
@@ -286,21 +280,65 @@ struct SolveShared {
     float red[kTile + 16 * kTile];
 };
 
-// c = T a_i for the support cache (T = L^-1 for PWLS, identity for LS).
-__device__ void cache_vector(const JobDev &J, int i, int slot) {
+// c = T a_i for the support cache (T = L^-1 for PWLS, identity for LS), and
+// its largest component magnitude (for the tensor-core operand scaling).
+__device__ void cache_vector(const JobDev &J, int i, int slot, double *sbuf) {
     const int p = J.p;
     const int im = i / J.n_l, il = i - im * J.n_l;
     float2 *c = J.cvec + (size_t)slot * p;
     const bool pwls = J.cost == IMG_COST_PWLS;
+    float mx = 0.f;
     for (int k = threadIdx.x; k < p; k += blockDim.x) {
+        float2 s = make_float2(0.f, 0.f);
         if (!pwls) {
-            c[k] = steer(J, il, im, k);
+            s = steer(J, il, im, k);
         } else {
-            float2 s = make_float2(0.f, 0.f);
             for (int l = 0; l <= k; ++l) cfma(s, J.Li32[(size_t)l * p + k], steer(J, il, im, l));
-            c[k] = s;
+        }
+        c[k] = s;
+        mx = fmaxf(mx, fmaxf(fabsf(s.x), fabsf(s.y)));
+    }
+    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) sbuf[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int w = 0; w < kThreads / 32; ++w) m = fmaxf(m, (float)sbuf[w]);
+        J.cmax[slot] = m;
+    }
+    __syncthreads();
+}
+
+// Power-of-two scale for the cached vectors of a list (max |entry| <= 1).
+__device__ float list_scale(const JobDev &J, const int *pos, int n, double *sbuf) {
+    float mx = 0.f;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) mx = fmaxf(mx, J.cmax[pos ? pos[j] : j]);
+    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) sbuf[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    mx = 0.f;
+    for (int w = 0; w < kThreads / 32; ++w) mx = fmaxf(mx, (float)sbuf[w]);
+    __syncthreads();
+    return mx > 0.f ? exp2f(-ceilf(log2f(mx))) : 1.f;
+}
+
+// K = base + sum_j wt[j] c_j c_j^H over a list of cached vectors, on tensor
+// cores when MODE != 0 and Kp = 64, else on CUDA cores.
+template <int MODE>
+__device__ void forward_cache(const JobDev &J, TcWork &T, const int *pos, const float *wt, int n,
+                              const float2 *base, bool base_identity, float2 *K, float2 *A,
+                              float *wsm, double *dbuf) {
+    if constexpr (MODE != 0) {
+        if (T.Kp == 64) {
+            constexpr bool BF = MODE == 2;
+            const float sX = list_scale(J, pos, n, dbuf);
+            tc_forward<BF>(T, J.p, n, wt, sX,
+                           [&](int t, int np) { tc_gen_X_cache<BF>(J, T, 0, pos, t * kTcM, np, sX); },
+                           base, base_identity, K, dbuf);
+            return;
         }
     }
+    forward_list(J, pos, wt, n, false, base, base_identity, K, A, wsm);
 }
 
 // Adjoint over a list of cached vectors: t_j = Re(c_j^H U c_j), handed to
@@ -321,16 +359,23 @@ __device__ void adjoint_list(const JobDev &J, const float2 *U, const int *pos, i
     } else {
         constexpr bool BF = MODE == 2;
         const float sB = tc_build_B<BF>(U, J.p, T, dbuf);
+        const float sXl = list_scale(J, pos, n, dbuf);
         const uint32_t idesc = idesc_f16(2 * T.Kp, BF ? 1 : 0);
-        for (int j0 = 0; j0 < n; j0 += kTcM) {
-            const int np = min(kTcM, n - j0);
-            const float sX = tc_gen_X_cache<BF>(J, T, pos, j0, np, dbuf);
-            tc_mma_tile(T, idesc);
-            tc_epilogue_cache(J, T, pos, j0, np, red);
-            const float inv = 1.f / (sX * sB);
-            if (threadIdx.x < np) epi(j0 + threadIdx.x, red[threadIdx.x] * inv);
-            __syncthreads();
-        }
+        tc_run_tiles(
+            T, (n + kTcM - 1) / kTcM, idesc,
+            [&](int t, int b) {
+                const int j0 = t * kTcM;
+                tc_gen_X_cache<BF>(J, T, b, pos, j0, min(kTcM, n - j0), sXl);
+                T.sX[b] = sXl;
+            },
+            [&](int t, int b) {
+                const int j0 = t * kTcM;
+                const int np = min(kTcM, n - j0);
+                tc_epilogue<BF>(T, b, red);
+                const float inv = 1.f / (T.sX[b] * T.sX[b] * sB);
+                if (threadIdx.x < np) epi(j0 + threadIdx.x, red[threadIdx.x] * inv);
+                __syncthreads();
+            });
     }
 }
 
@@ -355,16 +400,21 @@ __device__ void adjoint_full(const JobDev &J, const float2 *U, float2 *A, TcWork
         constexpr bool BF = MODE == 2;
         const float sB = tc_build_B<BF>(U, J.p, T, dbuf);
         const float sX = steer_scale(J.p);
-        const float inv = 1.f / (sX * sB);
+        const float inv = 1.f / (sX * sX * sB);
         const uint32_t idesc = idesc_f16(2 * T.Kp, BF ? 1 : 0);
-        for (int pix0 = 0; pix0 < Q; pix0 += kTcM) {
-            const int np = min(kTcM, Q - pix0);
-            tc_gen_X_steer<BF>(J, T, pix0, np, sX);
-            tc_mma_tile(T, idesc);
-            tc_epilogue_steer(J, T, pix0, np, red);
-            if (threadIdx.x < np) epi(pix0 + threadIdx.x, red[threadIdx.x] * inv);
-            __syncthreads();
-        }
+        tc_run_tiles(
+            T, (Q + kTcM - 1) / kTcM, idesc,
+            [&](int t, int b) {
+                const int pix0 = t * kTcM;
+                tc_gen_X_steer<BF>(J, T, b, pix0, min(kTcM, Q - pix0), sX);
+            },
+            [&](int t, int b) {
+                const int pix0 = t * kTcM;
+                const int np = min(kTcM, Q - pix0);
+                tc_epilogue<BF>(T, b, red);
+                if (threadIdx.x < np) epi(pix0 + threadIdx.x, red[threadIdx.x] * inv);
+                __syncthreads();
+            });
     }
 }
 
@@ -374,7 +424,7 @@ __device__ void adjoint_full(const JobDev &J, const float2 *U, float2 *A, TcWork
 // eq. lanczos; rotations and stopping tests as in the FP64 oracle, scalars
 // in FP64.  Returns the iteration count; the solution is in J.xs[0..f).
 template <int MODE>
-__device__ int lsqr_cta(const JobDev &J, int f, float2 *A, TcWork &T, SolveShared &S) {
+__device__ int lsqr_cta(const JobDev &J, int f, float2 *A, TcWork &T, SolveShared &S, DevInfo &info) {
     const int p = J.p, pp = p * p;
     float2 *u = J.W0;
     double acc = 0.0;
@@ -412,7 +462,9 @@ __device__ int lsqr_cta(const JobDev &J, int f, float2 *A, TcWork &T, SolveShare
         // u <- M v - alpha u
         for (int j = threadIdx.x; j < f; j += blockDim.x) wt[j] = J.scale[J.supp[fpos[j]]] * J.v[j];
         __syncthreads();
-        forward_list(J, fpos, wt, f, false, nullptr, false, J.W1, A, S.wsm);
+        long long tc0 = clock64();
+        forward_cache<MODE>(J, T, fpos, wt, f, nullptr, false, J.W1, A, S.wsm, S.dbuf);
+        info.cyc_lsqr_fwd += (double)(clock64() - tc0);
         acc = 0.0;
         const float fa = (float)alpha;
         for (int e = threadIdx.x; e < pp; e += blockDim.x) {
@@ -430,9 +482,11 @@ __device__ int lsqr_cta(const JobDev &J, int f, float2 *A, TcWork &T, SolveShare
         anorm2 += alpha * alpha + beta * beta;
         // v <- M^H u - beta v
         const float fb = (float)beta;
+        tc0 = clock64();
         adjoint_list<MODE>(J, u, fpos, f, A, T, S.red, S.dbuf, [&](int j, float t) {
             J.v[j] = J.scale[J.supp[fpos[j]]] * t - fb * J.v[j];
         });
+        info.cyc_lsqr_adj += (double)(clock64() - tc0);
         acc = 0.0;
         for (int j = threadIdx.x; j < f; j += blockDim.x) acc += (double)J.v[j] * J.v[j];
         alpha = sqrt(block_sum(acc, S.dbuf));
@@ -481,6 +535,7 @@ __device__ void supp_remove(const JobDev &J, int i, int &ns) {
         if (threadIdx.x == 0) {
             J.supp[sl] = moved;
             J.slot[moved] = sl;
+            J.cmax[sl] = J.cmax[last];
         }
     }
     if (threadIdx.x == 0) J.slot[i] = -1;
@@ -500,7 +555,7 @@ k_solve(JobDev *const *jobs, DevInfo *batch_info, double *const *sigma_out) {
         (reinterpret_cast<uintptr_t>(smem4) + 1023) & ~uintptr_t(1023));
     float2 *A = reinterpret_cast<float2 *>(dyn);
     __shared__ SolveShared S;
-    __shared__ uint64_t tc_bar;
+    __shared__ uint64_t tc_bar[2];
     __shared__ uint32_t tc_slot;
     DevInfo info{};
     info.status = IMG_OK;
@@ -517,13 +572,7 @@ k_solve(JobDev *const *jobs, DevInfo *batch_info, double *const *sigma_out) {
     TcWork T{};
     if constexpr (MODE != 0) {
         tc_carve(T, dyn, p);
-        T.bar = &tc_bar;
-        if (threadIdx.x == 0) mbar_init(&tc_bar, 1);
-        if (threadIdx.x < 32) tmem_alloc(&tc_slot, tc_tmem_cols(p));
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        T.tmem = tc_slot;
+        tc_setup(T, tc_bar, &tc_slot, p);
     }
     for (int i = threadIdx.x; i < Q; i += blockDim.x) {
         J.x[i] = 0.0;
@@ -564,10 +613,11 @@ k_solve(JobDev *const *jobs, DevInfo *batch_info, double *const *sigma_out) {
                     wt[j] = -J.scale[i] * (float)J.x[i];
                 }
                 __syncthreads();
-                forward_list(J, J.fpos + f, wt, nu, false, pwls ? nullptr : J.R32, pwls, J.W0, A, S.wsm);
+                forward_cache<MODE>(J, T, J.fpos + f, wt, nu, pwls ? nullptr : J.R32, pwls, J.W0, A, S.wsm,
+                                    S.dbuf);
                 info.op_flops += flops_fwd(p, nu);
                 const long long t0 = clock64();
-                const int its = lsqr_cta<MODE>(J, f, A, T, S);
+                const int its = lsqr_cta<MODE>(J, f, A, T, S, info);
                 info.cyc_lsqr += (double)(clock64() - t0);
                 info.lsqr_iters += its;
                 info.op_flops += (its + 1) * (flops_fwd(p, f) + flops_adj(p, f));
@@ -594,7 +644,8 @@ k_solve(JobDev *const *jobs, DevInfo *batch_info, double *const *sigma_out) {
                     wt[j] = -J.scale[i] * (float)J.x[i];
                 }
                 __syncthreads();
-                forward_list(J, nullptr, wt, ns, false, pwls ? nullptr : J.R32, pwls, J.W1, A, S.wsm);
+                forward_cache<MODE>(J, T, nullptr, wt, ns, pwls ? nullptr : J.R32, pwls, J.W1, A, S.wsm,
+                                    S.dbuf);
                 info.op_flops += flops_fwd(p, ns);
                 const float2 *Ug = J.W1;
                 if (pwls) {
@@ -670,7 +721,7 @@ k_solve(JobDev *const *jobs, DevInfo *batch_info, double *const *sigma_out) {
                     info.status = IMG_ENOMEM;
                     break;
                 }
-                cache_vector(J, i, ns);
+                cache_vector(J, i, ns, S.dbuf);
                 if (threadIdx.x == 0) {
                     J.supp[ns] = i;
                     J.slot[i] = ns;
@@ -686,9 +737,7 @@ k_solve(JobDev *const *jobs, DevInfo *batch_info, double *const *sigma_out) {
     if (!converged && info.status == IMG_OK) info.status = IMG_ENOTCONV;
     if constexpr (MODE != 0) {
         if (T.timeouts && info.status == IMG_OK) info.status = IMG_ETIMEOUT;
-        tc_fence_before();
-        __syncthreads();
-        if (threadIdx.x < 32) tmem_dealloc(T.tmem, tc_tmem_cols(p));
+        tc_teardown(T, p);
     }
     double *out = sigma_out ? sigma_out[blockIdx.x] : nullptr;
     int nf = 0, nu = 0;
@@ -781,6 +830,31 @@ __global__ void k_psi_partial(const JobDev *Jp, const float *wx, float2 *part, i
                 }
         }
     }
+}
+
+// Tensor-core Psi x: CTA b accumulates pixels [b*per, (b+1)*per) into its
+// partial matrix part[b] (Kp = 64).
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1) k_psi_partial_tc(const JobDev *Jp, const float *wx, float2 *part,
+                                                               int per) {
+    const JobDev &J = *Jp;
+    constexpr bool BF = MODE == 2;
+    extern __shared__ float4 smem4[];
+    unsigned char *dyn = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem4) + 1023) & ~uintptr_t(1023));
+    __shared__ uint64_t bars[2];
+    __shared__ uint32_t slot;
+    __shared__ double dbuf[kThreads / 32];
+    TcWork T{};
+    tc_carve(T, dyn, J.p);
+    tc_setup(T, bars, &slot, J.p);
+    const int i0 = blockIdx.x * per;
+    const int n = max(0, min(per, J.Q - i0));
+    const float sX = steer_scale(J.p);
+    tc_forward<BF>(T, J.p, n, wx + i0, sX,
+                   [&](int t, int np) { tc_gen_X_steer<BF>(J, T, 0, i0 + t * kTcM, np, sX); },
+                   nullptr, false, part + (size_t)blockIdx.x * J.p * J.p, dbuf);
+    tc_teardown(T, J.p);
 }
 
 __global__ void k_psi_reduce(const float2 *part, int nparts, int pp, double2 *Kout) {
@@ -908,8 +982,27 @@ cudaError_t launch_solve(JobDev *const *jobs, int n, int max_p, int mode, DevInf
 
 // Psi x over all pixels: nparts CTAs write partial p x p sums into `part`
 // (nparts * p * p float2 of scratch), reduced in a fixed order in FP64.
+template <int MODE>
+static cudaError_t launch_psi_tc_t(const JobDev *job_dev, const float *wx, float2 *part, int nparts, int Q,
+                                   int p, double2 *Kout, cudaStream_t st) {
+    const size_t sm = tc_smem_bytes(p) + 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_psi_partial_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int per = (Q + nparts - 1) / nparts;
+    per = ((per + kTcM - 1) / kTcM) * kTcM;
+    const int used = (Q + per - 1) / per;
+    k_psi_partial_tc<MODE><<<used, kThreads, sm, st>>>(job_dev, wx, part, per);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_psi_reduce<<<(p * p + 255) / 256, 256, 0, st>>>(part, used, p * p, Kout);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_psi(const JobDev *job_dev, const float *wx, float2 *part, int nparts, int Q,
-                       int p, double2 *Kout, cudaStream_t st) {
+                       int p, int mode, double2 *Kout, cudaStream_t st) {
+    const int Kp = (p + 31) / 32 * 32;
+    if (mode == 1 && Kp == 64) return launch_psi_tc_t<1>(job_dev, wx, part, nparts, Q, p, Kout, st);
+    if (mode == 2 && Kp == 64) return launch_psi_tc_t<2>(job_dev, wx, part, nparts, Q, p, Kout, st);
     const size_t sm = (size_t)p * kTile * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(k_psi_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;

@@ -152,14 +152,17 @@ __device__ __forceinline__ uint32_t sw128_off(int r, int c, int R) {
     return (uint32_t)(kb * R * 128 + (r >> 3) * 1024 + (r & 7) * 128 + ((cc ^ (r & 7)) << 4));
 }
 
-// Tensor-core workspace of one CTA.
+// Tensor-core workspace of one CTA: two X tiles and two accumulators so that
+// generating tile t+1 and the epilogue of tile t overlap the MMAs.
 struct TcWork {
-    unsigned char *Xhi, *Xlo, *Bhi, *Blo;  // 1024-aligned operand tiles
-    uint64_t *bar;                          // MMA completion barrier
-    uint32_t tmem;                          // accumulator base (lane 0, column 0)
-    uint32_t phase;                         // parity of the next completion
-    int Kp;                                 // p rounded up to 32
-    int timeouts;                           // bounded waits that ran out
+    unsigned char *Xhi[2], *Xlo[2];  // 1024-aligned operand tiles (pixels x 2Kp)
+    unsigned char *Bhi, *Blo;        // (2Kp x 2Kp)
+    uint64_t *bar;                   // two MMA completion barriers
+    uint32_t tmem;                   // accumulator base (lane 0, column 0)
+    uint32_t phase[2];               // parity of each barrier's next completion
+    float sX[2];                     // scale of the X tile in each buffer
+    int Kp;                          // p rounded up to 32
+    int timeouts;                    // bounded waits that ran out
 };
 
 // Bytes of shared memory the operand tiles need for p (plus 1024 alignment).
@@ -167,10 +170,12 @@ __host__ __device__ inline size_t tc_smem_bytes(int p) {
     const int Kp = (p + 31) / 32 * 32;
     const size_t x = (size_t)kTcM * 2 * Kp * 2;      // one 16-bit tile of X
     const size_t b = (size_t)2 * Kp * 2 * Kp * 2;    // one 16-bit tile of B
-    return 2 * x + 2 * b + 1024;
+    return 4 * x + 2 * b + 1024;
 }
+// Tensor-memory columns: three FP32 accumulators of 2Kp columns each (two
+// for the adjoint pipeline, one for the forward product).
 __host__ __device__ inline uint32_t tc_tmem_cols(int p) {
-    const int n = 2 * ((p + 31) / 32 * 32);
+    const int n = 6 * ((p + 31) / 32 * 32);
     uint32_t c = 32;
     while ((int)c < n) c <<= 1;
     return c;
@@ -181,10 +186,34 @@ __device__ inline void tc_carve(TcWork &T, unsigned char *base, int p) {
     T.Kp = (p + 31) / 32 * 32;
     const size_t x = (size_t)kTcM * 2 * T.Kp * 2;
     const size_t b = (size_t)2 * T.Kp * 2 * T.Kp * 2;
-    T.Xhi = base;
-    T.Xlo = base + x;
-    T.Bhi = base + 2 * x;
-    T.Blo = base + 2 * x + b;
+    T.Xhi[0] = base;
+    T.Xlo[0] = base + x;
+    T.Xhi[1] = base + 2 * x;
+    T.Xlo[1] = base + 3 * x;
+    T.Bhi = base + 4 * x;
+    T.Blo = base + 4 * x + b;
+    T.phase[0] = T.phase[1] = 0;
+    T.timeouts = 0;
+}
+
+// Set up barriers and tensor memory (all threads; warp 0 allocates).
+__device__ inline void tc_setup(TcWork &T, uint64_t *bars, uint32_t *slot, int p) {
+    T.bar = bars;
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+    }
+    if (threadIdx.x < 32) tmem_alloc(slot, tc_tmem_cols(p));
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    T.tmem = *slot;
+}
+
+__device__ inline void tc_teardown(TcWork &T, int p) {
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) tmem_dealloc(T.tmem, tc_tmem_cols(p));
 }
 
 // B = real embedding of U, scaled by a power of two to max |entry| <= 1,
@@ -241,48 +270,46 @@ __device__ float tc_build_B(const float2 *U, int p, TcWork &T, double *sbuf) {
     return sc;
 }
 
-// Issue the 3-product MMA chain for the current X/B tiles and wait for it.
-// Call with all threads after the operand writes (this function fences,
-// synchronises and waits).  Returns false if the wait ran out.
-__device__ inline bool tc_mma_tile(TcWork &T, uint32_t idesc) {
-    fence_async_smem();
-    __syncthreads();
+// Issue the 3-product MMA chain for X[b] against B into accumulator b and
+// commit it to barrier b (one thread).
+__device__ inline void tc_issue(const TcWork &T, int b, uint32_t idesc) {
     const int Kp = T.Kp, N = 2 * Kp, nks = (2 * Kp) / 16;
-    if (threadIdx.x == 0) {
-        tc_fence_after();
-        const uint32_t xh = smem_u32(T.Xhi), xl = smem_u32(T.Xlo);
-        const uint32_t bh = smem_u32(T.Bhi), bl = smem_u32(T.Blo);
-        for (int s = 0; s < nks; ++s) {
-            const uint32_t kb = s >> 2, off = (s & 3) * 32;
-            const uint32_t xo = kb * kTcM * 128 + off, bo = kb * N * 128 + off;
-            mma_f16(T.tmem, sw128_desc(xh + xo), sw128_desc(bh + bo), idesc, s > 0 ? 1u : 0u);
-            mma_f16(T.tmem, sw128_desc(xh + xo), sw128_desc(bl + bo), idesc, 1u);
-            mma_f16(T.tmem, sw128_desc(xl + xo), sw128_desc(bh + bo), idesc, 1u);
-        }
-        mma_commit(T.bar);
-    }
-    const bool ok = mbar_wait(T.bar, T.phase);
-    T.phase ^= 1u;
     tc_fence_after();
-    if (!ok) T.timeouts++;
-    return ok;
+    const uint32_t xh = smem_u32(T.Xhi[b]), xl = smem_u32(T.Xlo[b]);
+    const uint32_t bh = smem_u32(T.Bhi), bl = smem_u32(T.Blo);
+    const uint32_t d = T.tmem + (uint32_t)(b * N);
+    for (int s = 0; s < nks; ++s) {
+        const uint32_t kb = s >> 2, off = (s & 3) * 32;
+        const uint32_t xo = kb * kTcM * 128 + off, bo = kb * N * 128 + off;
+        mma_f16(d, sw128_desc(xh + xo), sw128_desc(bh + bo), idesc, s > 0 ? 1u : 0u);
+        mma_f16(d, sw128_desc(xh + xo), sw128_desc(bl + bo), idesc, 1u);
+        mma_f16(d, sw128_desc(xl + xo), sw128_desc(bh + bo), idesc, 1u);
+    }
+    mma_commit(&T.bar[b]);
 }
 
-// Epilogue of one tile: this thread's lane (pixel row r) and half (real or
-// imaginary columns) dotted with xh[0..Kp) (the thread's own x half, FP32,
-// zero beyond p).  Returns the partial sum; the caller adds both halves.
-__device__ inline float tc_dot_half(const TcWork &T, const float *xhalf) {
-    const int warp = threadIdx.x >> 5;
-    const int half = warp >> 2;
-    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-    float acc = 0.f;
-    for (int c0 = 0; c0 < T.Kp; c0 += 16) {
-        float d[16];
-        tmem_ld16(T.tmem + lane_base + (uint32_t)(half * T.Kp + c0), d);
-#pragma unroll
-        for (int q = 0; q < 16; ++q) acc = fmaf(xhalf[c0 + q], d[q], acc);
+// Software pipeline over tiles: gen(t, b) fills X[b] (and T.sX[b]) for tile
+// t, epi(t, b) consumes accumulator b.  Generating tile t+1 and the epilogue
+// of tile t run while the tensor cores work on the other buffer.  The B tile
+// must be in place before the call.  All threads call this.
+template <class Gen, class Epi>
+__device__ inline void tc_run_tiles(TcWork &T, int ntiles, uint32_t idesc, Gen gen, Epi epi) {
+    if (ntiles <= 0) return;
+    gen(0, 0);
+    fence_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) tc_issue(T, 0, idesc);
+    for (int t = 0; t < ntiles; ++t) {
+        const int b = t & 1;
+        if (t + 1 < ntiles) gen(t + 1, b ^ 1);
+        fence_async_smem();
+        if (!mbar_wait(&T.bar[b], T.phase[b])) T.timeouts++;
+        T.phase[b] ^= 1u;
+        tc_fence_after();
+        __syncthreads();
+        if (t + 1 < ntiles && threadIdx.x == 0) tc_issue(T, b ^ 1, idesc);
+        epi(t, b);
     }
-    return acc;
 }
 
 }  // namespace img
@@ -292,21 +319,41 @@ namespace img {
 // X tile (128 rows) from steering vectors of pixels pix0 .. pix0+np-1; rows
 // beyond np are zero.  Values scaled by sX (a power of two).
 template <bool BF16>
-__device__ inline void tc_gen_X_steer(const JobDev &J, TcWork &T, int pix0, int np, float sX) {
-    const int p = J.p, Kp = T.Kp, nc8 = Kp / 8;
+__device__ inline void tc_gen_X_steer(const JobDev &J, TcWork &T, int b, int pix0, int np, float sX) {
+    const int p = J.p, Kp = T.Kp, nc8 = Kp / 8, nl = J.n_l;
+    const float2 *__restrict__ El = J.El;
+    const float2 *__restrict__ Em = J.Em;
+    unsigned char *xh = T.Xhi[b], *xl = T.Xlo[b];
+    const bool vec = (p & 7) == 0;       // 64-byte aligned antenna chunks
     for (int it = threadIdx.x; it < kTcM * nc8; it += blockDim.x) {
         const int r = it / nc8, c8 = it - r * nc8;
         float re[8], im[8];
-        if (r < np) {
+        const int k0 = c8 * 8;
+        if (r < np && k0 < p) {
             const int i = pix0 + r;
-            const int mm = i / J.n_l, ll = i - mm * J.n_l;
+            const int mm = i / nl, ll = i - mm * nl;
+            if (vec) {
+                const float4 *e = reinterpret_cast<const float4 *>(El + (size_t)ll * p + k0);
+                const float4 *f = reinterpret_cast<const float4 *>(Em + (size_t)mm * p + k0);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int k = c8 * 8 + q;
-                float2 a = make_float2(0.f, 0.f);
-                if (k < p) a = steer(J, ll, mm, k);
-                re[q] = a.x * sX;
-                im[q] = a.y * sX;
+                for (int q = 0; q < 4; ++q) {
+                    const float4 x = __ldg(e + q), y = __ldg(f + q);
+                    const float2 a0 = cmul(make_float2(x.x, x.y), make_float2(y.x, y.y));
+                    const float2 a1 = cmul(make_float2(x.z, x.w), make_float2(y.z, y.w));
+                    re[2 * q] = a0.x * sX;
+                    im[2 * q] = a0.y * sX;
+                    re[2 * q + 1] = a1.x * sX;
+                    im[2 * q + 1] = a1.y * sX;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int k = k0 + q;
+                    float2 a = make_float2(0.f, 0.f);
+                    if (k < p) a = cmul(__ldg(El + (size_t)ll * p + k), __ldg(Em + (size_t)mm * p + k));
+                    re[q] = a.x * sX;
+                    im[q] = a.y * sX;
+                }
             }
         } else {
 #pragma unroll
@@ -315,117 +362,100 @@ __device__ inline void tc_gen_X_steer(const JobDev &J, TcWork &T, int pix0, int 
         uint4 hi, lo;
         split8<BF16>(re, hi, lo);
         uint32_t off = sw128_off(r, c8, kTcM);
-        *reinterpret_cast<uint4 *>(T.Xhi + off) = hi;
-        *reinterpret_cast<uint4 *>(T.Xlo + off) = lo;
+        *reinterpret_cast<uint4 *>(xh + off) = hi;
+        *reinterpret_cast<uint4 *>(xl + off) = lo;
         split8<BF16>(im, hi, lo);
         off = sw128_off(r, nc8 + c8, kTcM);
-        *reinterpret_cast<uint4 *>(T.Xhi + off) = hi;
-        *reinterpret_cast<uint4 *>(T.Xlo + off) = lo;
+        *reinterpret_cast<uint4 *>(xh + off) = hi;
+        *reinterpret_cast<uint4 *>(xl + off) = lo;
     }
 }
 
 // X tile from cached vectors cvec[pos[j0 + r]] (pos == nullptr: j0 + r),
-// scaled by a power of two to max |entry| <= 1.  Returns the scale.
+// scaled by sX (a power of two keeping every entry within unit range).
 template <bool BF16>
-__device__ inline float tc_gen_X_cache(const JobDev &J, TcWork &T, const int *pos, int j0, int np,
-                                       double *sbuf) {
+__device__ inline void tc_gen_X_cache(const JobDev &J, TcWork &T, int b, const int *pos, int j0, int np,
+                                      float sX) {
     const int p = J.p, Kp = T.Kp, nc8 = Kp / 8;
-    float mx = 0.f;
-    for (int e = threadIdx.x; e < np * p; e += blockDim.x) {
-        const int r = e / p, k = e - r * p;
-        const int sl = pos ? pos[j0 + r] : j0 + r;
-        const float2 c = J.cvec[(size_t)sl * p + k];
-        mx = fmaxf(mx, fmaxf(fabsf(c.x), fabsf(c.y)));
-    }
-    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) sbuf[threadIdx.x >> 5] = mx;
-    __syncthreads();
-    mx = 0.f;
-    for (int w = 0; w < kThreads / 32; ++w) mx = fmaxf(mx, (float)sbuf[w]);
-    __syncthreads();
-    const float sX = mx > 0.f ? exp2f(-ceilf(log2f(mx))) : 1.f;
+    unsigned char *xh = T.Xhi[b], *xl = T.Xlo[b];
+    const bool vec = (p & 7) == 0;
     for (int it = threadIdx.x; it < kTcM * nc8; it += blockDim.x) {
         const int r = it / nc8, c8 = it - r * nc8;
         float re[8], im[8];
+        const int k0 = c8 * 8;
         const int sl = r < np ? (pos ? pos[j0 + r] : j0 + r) : -1;
+        if (sl >= 0 && k0 < p) {
+            const float2 *c = J.cvec + (size_t)sl * p + k0;
+            if (vec) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int k = c8 * 8 + q;
-            float2 c = make_float2(0.f, 0.f);
-            if (sl >= 0 && k < p) c = J.cvec[(size_t)sl * p + k];
-            re[q] = c.x * sX;
-            im[q] = c.y * sX;
+                for (int q = 0; q < 4; ++q) {
+                    const float4 x = reinterpret_cast<const float4 *>(c)[q];
+                    re[2 * q] = x.x * sX;
+                    im[2 * q] = x.y * sX;
+                    re[2 * q + 1] = x.z * sX;
+                    im[2 * q + 1] = x.w * sX;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float2 x = (k0 + q < p) ? c[q] : make_float2(0.f, 0.f);
+                    re[q] = x.x * sX;
+                    im[q] = x.y * sX;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) re[q] = im[q] = 0.f;
         }
         uint4 hi, lo;
         split8<BF16>(re, hi, lo);
         uint32_t off = sw128_off(r, c8, kTcM);
-        *reinterpret_cast<uint4 *>(T.Xhi + off) = hi;
-        *reinterpret_cast<uint4 *>(T.Xlo + off) = lo;
+        *reinterpret_cast<uint4 *>(xh + off) = hi;
+        *reinterpret_cast<uint4 *>(xl + off) = lo;
         split8<BF16>(im, hi, lo);
         off = sw128_off(r, nc8 + c8, kTcM);
-        *reinterpret_cast<uint4 *>(T.Xhi + off) = hi;
-        *reinterpret_cast<uint4 *>(T.Xlo + off) = lo;
+        *reinterpret_cast<uint4 *>(xh + off) = hi;
+        *reinterpret_cast<uint4 *>(xl + off) = lo;
     }
-    return sX;
 }
 
-// Epilogue dot for a steering tile: thread's pixel row and half; red[256]
-// receives partial sums, red[r] (r < 128) the tile's outputs after the call
-// (unscaled by 1/(sX sB): the caller applies it).
-__device__ inline void tc_epilogue_steer(const JobDev &J, const TcWork &T, int pix0, int np,
-                                         float *red) {
+// Epilogue of one tile: thread (row r = pixel, half h = real / imaginary
+// columns) forms sum_k xs_k D[r][h Kp + k], with xs = hi + lo rebuilt from the
+// operand tile in shared memory (the scaled x the MMA consumed; conflict-free
+// 16-byte reads).  red[r] (r < 128) holds the tile's sums after the call; the
+// caller multiplies by 1/(sX^2 sB).
+template <bool BF16>
+__device__ inline void tc_epilogue(const TcWork &T, int b, float *red) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int half = warp >> 2, r = 32 * (warp & 3) + lane;
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-    const int p = J.p;
-    int ll = 0, mm = 0;
-    if (r < np) {
-        const int i = pix0 + r;
-        mm = i / J.n_l;
-        ll = i - mm * J.n_l;
-    }
+    const int nc8 = T.Kp / 8;
     float acc = 0.f;
     for (int c0 = 0; c0 < T.Kp; c0 += 16) {
         float d[16];
-        tmem_ld16(T.tmem + lane_base + (uint32_t)(half * T.Kp + c0), d);
-        if (r < np) {
+        tmem_ld16(T.tmem + lane_base + (uint32_t)(b * 2 * T.Kp + half * T.Kp + c0), d);
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const int k = c0 + q;
-                if (k < p) {
-                    const float2 a = steer(J, ll, mm, k);
-                    acc = fmaf(half ? a.y : a.x, d[q], acc);
-                }
-            }
-        }
-    }
-    red[half * kTcM + r] = acc;
-    __syncthreads();
-    if (threadIdx.x < kTcM) red[threadIdx.x] = red[threadIdx.x] + red[kTcM + threadIdx.x];
-    tc_fence_before();
-    __syncthreads();
-}
-
-// Epilogue dot for a cached-vector tile.
-__device__ inline void tc_epilogue_cache(const JobDev &J, const TcWork &T, const int *pos, int j0,
-                                         int np, float *red) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int half = warp >> 2, r = 32 * (warp & 3) + lane;
-    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-    const int p = J.p;
-    const int sl = r < np ? (pos ? pos[j0 + r] : j0 + r) : -1;
-    float acc = 0.f;
-    for (int c0 = 0; c0 < T.Kp; c0 += 16) {
-        float d[16];
-        tmem_ld16(T.tmem + lane_base + (uint32_t)(half * T.Kp + c0), d);
-        if (sl >= 0) {
+        for (int s8 = 0; s8 < 2; ++s8) {
+            const uint32_t off = sw128_off(r, half * nc8 + c0 / 8 + s8, kTcM);
+            const uint4 h4 = *reinterpret_cast<const uint4 *>(T.Xhi[b] + off);
+            const uint4 l4 = *reinterpret_cast<const uint4 *>(T.Xlo[b] + off);
+            const uint32_t hw[4] = {h4.x, h4.y, h4.z, h4.w}, lw[4] = {l4.x, l4.y, l4.z, l4.w};
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const int k = c0 + q;
-                if (k < p) {
-                    const float2 c = J.cvec[(size_t)sl * p + k];
-                    acc = fmaf(half ? c.y : c.x, d[q], acc);
+            for (int q = 0; q < 4; ++q) {
+                float h0, h1, l0, l1;
+                if (BF16) {
+                    h0 = __uint_as_float(hw[q] << 16);
+                    h1 = __uint_as_float(hw[q] & 0xffff0000u);
+                    l0 = __uint_as_float(lw[q] << 16);
+                    l1 = __uint_as_float(lw[q] & 0xffff0000u);
+                } else {
+                    h0 = __half2float(__ushort_as_half((unsigned short)(hw[q] & 0xffffu)));
+                    h1 = __half2float(__ushort_as_half((unsigned short)(hw[q] >> 16)));
+                    l0 = __half2float(__ushort_as_half((unsigned short)(lw[q] & 0xffffu)));
+                    l1 = __half2float(__ushort_as_half((unsigned short)(lw[q] >> 16)));
                 }
+                acc = fmaf(h0 + l0, d[s8 * 8 + 2 * q], acc);
+                acc = fmaf(h1 + l1, d[s8 * 8 + 2 * q + 1], acc);
             }
         }
     }
@@ -437,5 +467,165 @@ __device__ inline void tc_epilogue_cache(const JobDev &J, const TcWork &T, const
 }
 
 __device__ __forceinline__ float steer_scale(int p) { return exp2f(floorf(0.5f * log2f((float)p))); }
+
+}  // namespace img
+
+namespace img {
+
+// ---------------------------------------------------------------- forward
+// Forward operator on tensor cores: G = sum_j w_j x_j x_j^T (2Kp x 2Kp real),
+// from which K = sum_j w_j c_j c_j^H follows as
+//   Re K(a,b) = G(a,b) + G(Kp+a, Kp+b),  Im K(a,b) = G(Kp+a, b) - G(a, Kp+b).
+// The contraction runs over pixels, so the pixel-major X tiles of the adjoint
+// serve directly as MN-major operands: A = X_w^T (rows scaled by w_j), B = X^T.
+// In the MN-major 128-byte-swizzled reading of those tiles, 64 consecutive
+// MN elements form one 128-byte row, 8 rows (8 pixels, the K direction) form
+// a 1024-byte atom (SBO = 1024), and the next 64 MN elements sit one column
+// block further (LBO = 128 rows x 128 bytes).
+
+__device__ __forceinline__ uint64_t sw128_desc_mn(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// kind::f16 instruction descriptor with both operands MN-major, M = N = n.
+__host__ __device__ constexpr uint32_t idesc_f16_mn(int n, int ab_fmt) {
+    return (1u << 4) | ((uint32_t)ab_fmt << 7) | ((uint32_t)ab_fmt << 10) | (1u << 15) | (1u << 16) |
+           ((uint32_t)(n >> 3) << 17) | ((uint32_t)(n >> 4) << 24);
+}
+
+// Weighted copy of the pixel-major tile in buffer 0 into buffer 1:
+// Xw[j][.] = sW * w_j * X[j][.], re-split into hi/lo (rows j >= np are zero).
+template <bool BF16>
+__device__ inline void tc_weight_rows(TcWork &T, const float *w, int np, float sW) {
+    const int nch = 2 * T.Kp / 8;
+    for (int it = threadIdx.x; it < kTcM * nch; it += blockDim.x) {
+        const int r = it / nch, c = it - r * nch;
+        const uint32_t off = sw128_off(r, c, kTcM);
+        const uint4 h4 = *reinterpret_cast<const uint4 *>(T.Xhi[0] + off);
+        const uint4 l4 = *reinterpret_cast<const uint4 *>(T.Xlo[0] + off);
+        const uint32_t hw[4] = {h4.x, h4.y, h4.z, h4.w}, lw[4] = {l4.x, l4.y, l4.z, l4.w};
+        const float wr = r < np ? sW * w[r] : 0.f;
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float h0, h1, l0, l1;
+            if (BF16) {
+                h0 = __uint_as_float(hw[q] << 16);
+                h1 = __uint_as_float(hw[q] & 0xffff0000u);
+                l0 = __uint_as_float(lw[q] << 16);
+                l1 = __uint_as_float(lw[q] & 0xffff0000u);
+            } else {
+                h0 = __half2float(__ushort_as_half((unsigned short)(hw[q] & 0xffffu)));
+                h1 = __half2float(__ushort_as_half((unsigned short)(hw[q] >> 16)));
+                l0 = __half2float(__ushort_as_half((unsigned short)(lw[q] & 0xffffu)));
+                l1 = __half2float(__ushort_as_half((unsigned short)(lw[q] >> 16)));
+            }
+            v[2 * q] = wr * (h0 + l0);
+            v[2 * q + 1] = wr * (h1 + l1);
+        }
+        uint4 hi, lo;
+        split8<BF16>(v, hi, lo);
+        *reinterpret_cast<uint4 *>(T.Xhi[1] + off) = hi;
+        *reinterpret_cast<uint4 *>(T.Xlo[1] + off) = lo;
+    }
+}
+
+// Accumulate X_w^T X of the current tile pair (buffers 1 and 0) into the
+// forward accumulator (tensor-memory columns 4Kp .. 6Kp).  One thread.
+__device__ inline void tc_issue_fwd(const TcWork &T, uint32_t idesc, bool first) {
+    const int N = 2 * T.Kp;
+    tc_fence_after();
+    const uint32_t ah = smem_u32(T.Xhi[1]), al = smem_u32(T.Xlo[1]);
+    const uint32_t bh = smem_u32(T.Xhi[0]), bl = smem_u32(T.Xlo[0]);
+    const uint32_t d = T.tmem + (uint32_t)(2 * N);
+    const uint32_t lbo = kTcM * 128, sbo = 1024;
+    for (int s = 0; s < kTcM / 16; ++s) {
+        const uint32_t o = s * 2048;
+        mma_f16(d, sw128_desc_mn(ah + o, lbo, sbo), sw128_desc_mn(bh + o, lbo, sbo), idesc,
+                (first && s == 0) ? 0u : 1u);
+        mma_f16(d, sw128_desc_mn(ah + o, lbo, sbo), sw128_desc_mn(bl + o, lbo, sbo), idesc, 1u);
+        mma_f16(d, sw128_desc_mn(al + o, lbo, sbo), sw128_desc_mn(bh + o, lbo, sbo), idesc, 1u);
+    }
+    mma_commit(&T.bar[0]);
+}
+
+// Read the forward accumulator into shared memory G (2Kp x 2Kp FP32, row m
+// at stride 2Kp + 1 against bank conflicts), reusing the operand buffers.
+// All threads.
+__device__ inline float *tc_read_fwd(const TcWork &T) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int half = warp >> 2, m = 32 * (warp & 3) + lane;
+    const int N = 2 * T.Kp;
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    float *G = reinterpret_cast<float *>(T.Xhi[0]);
+    for (int c0 = 0; c0 < T.Kp; c0 += 16) {
+        float d[16];
+        tmem_ld16(T.tmem + lane_base + (uint32_t)(2 * N + half * T.Kp + c0), d);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) G[m * (N + 1) + half * T.Kp + c0 + q] = d[q];
+    }
+    tc_fence_before();
+    __syncthreads();
+    return G;
+}
+
+// Power-of-two scale taking max |w_j| (j < n) to at most 1 (all threads).
+__device__ inline float pow2_scale_of(const float *w, int n, double *sbuf) {
+    float mx = 0.f;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) mx = fmaxf(mx, fabsf(w[j]));
+    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) sbuf[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    mx = 0.f;
+    for (int w2 = 0; w2 < kThreads / 32; ++w2) mx = fmaxf(mx, (float)sbuf[w2]);
+    __syncthreads();
+    return mx > 0.f ? exp2f(-ceilf(log2f(mx))) : 1.f;
+}
+
+}  // namespace img
+
+namespace img {
+
+// Forward driver: K = base + sum_j wt[j] c_j c_j^H over n list entries whose
+// unweighted pixel-major tiles gen0(t, np) writes into buffer 0 (scaled by
+// sX).  Needs Kp = 64 (M = N = 128).  K: p x p complex, global memory.
+template <bool BF16, class Gen0>
+__device__ void tc_forward(TcWork &T, int p, int n, const float *wt, float sX, Gen0 gen0,
+                           const float2 *base, bool base_identity, float2 *K, double *dbuf) {
+    const float sW = pow2_scale_of(wt, n, dbuf);
+    const int N = 2 * T.Kp;
+    const uint32_t idesc = idesc_f16_mn(N, BF16 ? 1 : 0);
+    const int ntiles = (n + kTcM - 1) / kTcM;
+    for (int t = 0; t < ntiles; ++t) {
+        const int np = min(kTcM, n - t * kTcM);
+        gen0(t, np);
+        __syncthreads();
+        tc_weight_rows<BF16>(T, wt + t * kTcM, np, sW);
+        fence_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) tc_issue_fwd(T, idesc, t == 0);
+        if (!mbar_wait(&T.bar[0], T.phase[0])) T.timeouts++;
+        T.phase[0] ^= 1u;
+        tc_fence_after();
+        __syncthreads();
+    }
+    const float *G = ntiles ? tc_read_fwd(T) : nullptr;
+    const float inv = 1.f / (sX * sX * sW);
+    const int ld = N + 1, Kp = T.Kp;
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        const int bcol = e / p, a = e - bcol * p;
+        float kr = 0.f, ki = 0.f;
+        if (G) {
+            kr = (G[a * ld + bcol] + G[(Kp + a) * ld + Kp + bcol]) * inv;
+            ki = (G[(Kp + a) * ld + bcol] - G[a * ld + Kp + bcol]) * inv;
+        }
+        float2 bb = make_float2(0.f, 0.f);
+        if (base) bb = base[e];
+        else if (base_identity && a == bcol) bb = make_float2(1.f, 0.f);
+        K[e] = make_float2(bb.x + kr, bb.y + ki);
+    }
+    __syncthreads();
+}
 
 }  // namespace img

@@ -54,8 +54,9 @@ def test_dirty_and_mvdr_match_oracle(G, shape, prec):
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2])
-def test_psi_pair_matches_explicit_khatri_rao(G, prec):
-    job = synth.custom(5, 9, 10, 7, 2, 400, radius=3.0)
+@pytest.mark.parametrize("p", [9, 48, 64])
+def test_psi_pair_matches_explicit_khatri_rao(G, prec, p):
+    job = synth.custom(5, p, 21, 13, 2, 400 + 4 * p, radius=3.0)
     A, Psi = _oracle_ops(job)
     im = G.Imager.from_job(job, precision=prec)
     rng = np.random.default_rng(1)
