@@ -213,6 +213,26 @@ img_status img_prepare_batch(img_ctx *const *ctxs, int n);
 img_status img_solve_batch(img_ctx *const *ctxs, int n, double *const *sigma,
                            img_solve_info *infos, int on_device);
 
+/* Forward operator K = Psi x (as img_psi with IMG_PREC_FP32) for callers
+ * that cannot allocate device memory - code inside a host framework whose
+ * allocator owns the GPU's memory, or a real-time loop that must not hit
+ * cudaMalloc's implicit synchronisation.  The paper has no counterpart: it is
+ * a deployment variant.  No context is needed and nothing is allocated: the
+ * steering tables and split-K partial sums live in one static device array
+ * of 2.25 MiB that every GPU loading the library holds until exit.
+ *   p <= 64, n_l <= 256, n_m <= 256, n_l * n_m <= 65536; larger sizes give
+ *   IMG_ENOMEM (beyond the fixed capacity), bad arguments IMG_EINVAL.
+ *   ant_xyz (p x 3 row-major, z ignored), l (n_l), m (n_m), x (Q doubles):
+ *   device memory.  Kout: device memory, p x p complex128 column-major.
+ *   stream: cudaStream_t or NULL; the call synchronises it before returning.
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture.  Every call
+ * reuses the same array: calls that overlap on the GPU (other streams or
+ * threads) race with each other; serialise them. */
+img_status img_psi_noalloc(int p, int n_l, int n_m, const double *ant_xyz, const double *l,
+                           const double *m, double lambda, const double *x, double *Kout,
+                           void *stream);
+
 /* Release all device memory of ctx.  NULL is allowed. */
 void img_destroy(img_ctx *ctx);
 

@@ -24,8 +24,8 @@ SET_L, SET_U, SET_F = 0, 1, 2
 EXPORTS = ("img_params_default", "img_create", "img_set_covariance", "img_dirty",
            "img_mvdr_bound", "img_solve", "img_get_sets", "img_get_gradient", "img_get_events",
            "img_psi",
-           "img_psi_adj", "img_prepare_batch", "img_solve_batch", "img_destroy",
-           "img_status_str")
+           "img_psi_adj", "img_prepare_batch", "img_solve_batch", "img_psi_noalloc",
+           "img_destroy", "img_status_str")
 
 
 class ImgParams(C.Structure):
@@ -101,6 +101,8 @@ def load(build_if_missing: bool = False) -> C.CDLL:
     lib.img_prepare_batch.restype = i
     lib.img_solve_batch.argtypes = [C.POINTER(vp), i, C.POINTER(dp), C.POINTER(SolveInfo), i]
     lib.img_solve_batch.restype = i
+    lib.img_psi_noalloc.argtypes = [i, i, i, dp, dp, dp, C.c_double, dp, dp, vp]
+    lib.img_psi_noalloc.restype = i
     lib.img_destroy.argtypes = [vp]
     lib.img_destroy.restype = None
     lib.img_status_str.argtypes = [i]
@@ -251,6 +253,15 @@ class Imager:
         out = np.empty(self.Q, dtype=np.float64)
         _check(self._lib.img_psi_adj(self.h, U.ctypes.data, out.ctypes.data, 0), "img_psi_adj")
         return out
+
+
+def psi_noalloc(p, n_l, n_m, ant_xyz, l, m, lam, x, Kout, stream=0):
+    """Allocation-free forward operator; every array argument is a device
+    pointer (torch CUDA tensor or integer address).  Returns the status."""
+    lib = load()
+    a = [v if isinstance(v, int) else _ptr(v) for v in (ant_xyz, l, m, x, Kout)]
+    return lib.img_psi_noalloc(int(p), int(n_l), int(n_m), a[0], a[1], a[2], float(lam), a[3], a[4],
+                               C.c_void_p(int(stream)) if stream else None)
 
 
 def prepare_batch(imagers):

@@ -186,7 +186,7 @@ __device__ __forceinline__ void fill_cache_adj(const JobDev &J, const int *pos, 
 // Entries come from the support cache (pos[j] or j) or, when gen != 0, are
 // steering vectors of pixels j (pos ignored, weights wt[j] per pixel).
 // C: shared chunk of kTile * p float2 laid out [j][k]; wsm: kTile floats.
-__device__ void forward_list(const JobDev &J, const int *pos, const float *wt, int n, bool gen,
+__device__ inline void forward_list(const JobDev &J, const int *pos, const float *wt, int n, bool gen,
                              const float2 *base, bool base_identity, float2 *K, float2 *C,
                              float *wsm) {
     const int p = J.p;
@@ -263,7 +263,7 @@ __device__ void forward_list(const JobDev &J, const int *pos, const float *wt, i
 // C = op(A) * B for p x p complex column-major matrices in global memory
 // (plain loads: the operands may have been written earlier in the same kernel).
 // op(A) = A (conjA = false) or A^H (conjA = true).  C must not alias A or B.
-__device__ void cgemm_pp(int p, const float2 *A, bool conjA, const float2 *B, float2 *Cm) {
+__device__ inline void cgemm_pp(int p, const float2 *A, bool conjA, const float2 *B, float2 *Cm) {
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     for (int mt = 0; mt < p; mt += kTile) {
         for (int nt = 0; nt < p; nt += kTile) {
