@@ -98,9 +98,20 @@ def sm_count() -> int:
     return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
 
 
+PRECISIONS = {"fp32": 0, "f16x3": 1, "bf16x3": 2}
+
+
 def fp32_alu_peak_tflops(sms: int, mhz: float) -> float:
     """FP32 CUDA-core peak: 128 FMA lanes per SM, 2 flops each."""
     return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
 
 
 def run_ours(args, rank: int, world: int):
@@ -110,10 +121,12 @@ def run_ours(args, rank: int, world: int):
     G.load()
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    B = args.batch or sm_count()
+    B = args.batch or 2 * sm_count()
     jobs = make_jobs(B, 2000 + 100_000 * rank)
     stream = torch.cuda.Stream(device=dev)
-    ims = [G.Imager(j.ant_xyz, j.l, j.m, j.lam, stream=stream.cuda_stream) for j in jobs]
+    prec = PRECISIONS[args.precision]
+    ims = [G.Imager(j.ant_xyz, j.l, j.m, j.lam, stream=stream.cuda_stream, precision=prec)
+           for j in jobs]
     # column-major complex128 bytes of each R_hat, resident on the device
     R_dev = [torch.from_numpy(np.ascontiguousarray(j.R.ravel(order="F"))).to(dev) for j in jobs]
     sig_dev = [torch.empty(j.Q, dtype=torch.float64, device=dev) for j in jobs]
@@ -151,6 +164,7 @@ def run_ours(args, rank: int, world: int):
         torch.cuda.synchronize()
         clocks = clk.stop()
     t_step = [e0.elapsed_time(e2) / 1e3 for e0, _, e2 in ev]
+    t_prep = [e0.elapsed_time(e1) / 1e3 for e0, e1, _ in ev]
     t_solve = [e1.elapsed_time(e2) / 1e3 for _, e1, e2 in ev]
     total = sum(t_step)
     if world > 1:
@@ -191,7 +205,8 @@ def run_ours(args, rank: int, world: int):
         im.close()
 
     res = {
-        "B": B, "total": total, "t_step": t_step, "t_solve": t_solve, "flops": flops,
+        "B": B, "total": total, "t_step": t_step, "t_solve": t_solve, "t_prep": t_prep,
+        "prep_flops": float(sum(2 * 8.0 * j.p * j.p * j.Q for j in jobs)), "flops": flops,
         "conv": conv, "outer": outer, "clocks": clocks, "e2e": e2e,
         "sms": sm_count(),
     }
@@ -275,7 +290,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--batch", type=int, default=0, help="images per step (0: one per SM)")
+    ap.add_argument("--batch", type=int, default=0, help="images per step (0: two per SM)")
+    ap.add_argument("--precision", default="f16x3", choices=sorted(PRECISIONS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -299,25 +315,39 @@ def main():
         total = r["total"]
         value = world * B * K / total
         t_solve = float(np.mean(r["t_solve"]))
+        t_prep = float(np.mean(r["t_prep"]))
         flops = float(np.mean(r["flops"]))
         mhz = r["clocks"]["sm_max_mhz"] or 2070.0
-        peak = fp32_alu_peak_tflops(r["sms"], mhz)
         achieved = flops / t_solve / 1e12
+        pk = measured_peaks()
+        if args.precision == "fp32":
+            bound, peak = "alu", fp32_alu_peak_tflops(r["sms"], mhz)
+            basis = f"FP32 CUDA cores: {r['sms']} SMs x 128 lanes x 2 flops x {mhz:.0f} MHz"
+        else:
+            bound = "tensor"
+            if pk.get("bf16_tflops_sustained"):
+                peak = float(pk["bf16_tflops_sustained"])
+                basis = ("measured dense BF16 tensor peak, sustained (FP16 runs at the BF16 rate); "
+                         "achieved counts algorithmic flops, the split products execute 3x")
+            else:
+                peak = 1700.0
+                basis = "fallback sustained BF16 tensor peak (no measured peaks file)"
         line = {
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": total / K * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else f"{args.precision}+f32acc",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "batch_per_gpu": B, "n_l": 128, "n_m": 128, "p": 64,
-                       "cost": "pwls", "bound": "mvdr", "precision": "fp32",
+                       "cost": "pwls", "bound": "mvdr", "precision": args.precision,
                        "l2": "flushed between steps (512 MB write)",
                        "parallelism": f"dp{world} (independent images)"},
-            "roofline": {"kernel": "k_solve", "bound": "alu", "achieved": achieved, "peak": peak,
+            "roofline": {"kernel": "k_solve", "bound": bound, "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "peak_basis": f"FP32 CUDA cores: {r['sms']} SMs x 128 lanes x 2 flops "
-                                       f"x {mhz:.0f} MHz"},
+                         "peak_basis": basis},
             "solve_ms_per_step": t_solve * 1e3,
-            "op_tflops": achieved,
+            "prepare_ms_per_step": t_prep * 1e3,
+            "prepare_tflops": r["prep_flops"] / t_prep / 1e12,
             "converged": r["conv"], "mean_outer_passes": r["outer"],
             "gpu_launches": 4 * K,
             "clocks": r["clocks"],

@@ -98,6 +98,7 @@ size_t carve(img_ctx *c, char *base) {
     J.fpos = cv.take<int>(cap);
     J.v = cv.take<float>(cap);
     J.w = cv.take<float>(cap);
+    J.sF = cv.take<float>(cap);
     J.xs = cv.take<float>(2 * (size_t)cap);
     J.W0 = cv.take<float2>(pp);
     J.W1 = cv.take<float2>(pp);

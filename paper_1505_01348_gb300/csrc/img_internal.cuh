@@ -67,6 +67,7 @@ struct JobDev {
     float *cmax;           // cap, max over k of |Re c_i[k]|, |Im c_i[k]|
     int *fpos;             // cap, positions in supp of the free pixels
     float *v, *w, *xs;     // cap, LSQR vectors indexed by F position
+    float *sF;             // cap, s_i of the free pixels in F order (per LSQR solve)
     float2 *W0, *W1, *W2;  // p*p scratch matrices
     // decision log (Table I order): kind << 24 | pixel, and lambda or mu
     int *ev;

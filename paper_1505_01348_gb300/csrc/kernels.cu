@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bounds_tc(JobDev *const *jobs) 
     tc_setup(T, bars, &slot, J.p);
     const float sX = steer_scale(J.p);
     const uint32_t idesc = idesc_f16(2 * T.Kp, BF ? 1 : 0);
-    const int ntiles = (J.Q + kTcM - 1) / kTcM;
+    const int ntiles = tc_num_tiles(J.n_l, J.n_m);
     const int mine = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     for (int pass = 0; pass < 2; ++pass) {
         const float sB = tc_build_B<BF>(pass == 0 ? J.R32 : J.Ri32, J.p, T, dbuf);
@@ -170,15 +170,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_bounds_tc(JobDev *const *jobs) 
         float *dst = pass == 0 ? J.dirty : J.h;
         tc_run_tiles(
             T, mine, idesc,
+            [&](int t, int b) { tc_gen_X_steer<BF>(J, T, b, blockIdx.x + t * gridDim.x, sX); },
             [&](int t, int b) {
-                const int pix0 = (blockIdx.x + t * gridDim.x) * kTcM;
-                tc_gen_X_steer<BF>(J, T, b, pix0, min(kTcM, J.Q - pix0), sX);
-            },
-            [&](int t, int b) {
-                const int pix0 = (blockIdx.x + t * gridDim.x) * kTcM;
-                const int np = min(kTcM, J.Q - pix0);
                 tc_epilogue<BF>(T, b, red);
-                if (threadIdx.x < np) dst[pix0 + threadIdx.x] = red[threadIdx.x] * inv;
+                if (threadIdx.x < kTcM) {
+                    const int i = tc_tile_pixel(blockIdx.x + t * gridDim.x, threadIdx.x, J.n_l, J.n_m);
+                    if (i >= 0) dst[i] = red[threadIdx.x] * inv;
+                }
                 __syncthreads();
             });
     }
@@ -206,19 +204,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_psi_adj_tc(const JobDev *Jp, co
     const uint32_t idesc = idesc_f16(2 * T.Kp, BF ? 1 : 0);
     const float sB = tc_build_B<BF>(U, J.p, T, dbuf);
     const float inv = 1.f / (sX * sX * sB);
-    const int ntiles = (J.Q + kTcM - 1) / kTcM;
+    const int ntiles = tc_num_tiles(J.n_l, J.n_m);
     const int mine = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     tc_run_tiles(
         T, mine, idesc,
+        [&](int t, int b) { tc_gen_X_steer<BF>(J, T, b, blockIdx.x + t * gridDim.x, sX); },
         [&](int t, int b) {
-            const int pix0 = (blockIdx.x + t * gridDim.x) * kTcM;
-            tc_gen_X_steer<BF>(J, T, b, pix0, min(kTcM, J.Q - pix0), sX);
-        },
-        [&](int t, int b) {
-            const int pix0 = (blockIdx.x + t * gridDim.x) * kTcM;
-            const int np = min(kTcM, J.Q - pix0);
             tc_epilogue<BF>(T, b, red);
-            if (threadIdx.x < np) out[pix0 + threadIdx.x] = red[threadIdx.x] * inv;
+            if (threadIdx.x < kTcM) {
+                const int i = tc_tile_pixel(blockIdx.x + t * gridDim.x, threadIdx.x, J.n_l, J.n_m);
+                if (i >= 0) out[i] = red[threadIdx.x] * inv;
+            }
             __syncthreads();
         });
     tc_teardown(T, J.p);
@@ -403,16 +399,14 @@ __device__ void adjoint_full(const JobDev &J, const float2 *U, float2 *A, TcWork
         const float inv = 1.f / (sX * sX * sB);
         const uint32_t idesc = idesc_f16(2 * T.Kp, BF ? 1 : 0);
         tc_run_tiles(
-            T, (Q + kTcM - 1) / kTcM, idesc,
+            T, tc_num_tiles(J.n_l, J.n_m), idesc,
+            [&](int t, int b) { tc_gen_X_steer<BF>(J, T, b, t, sX); },
             [&](int t, int b) {
-                const int pix0 = t * kTcM;
-                tc_gen_X_steer<BF>(J, T, b, pix0, min(kTcM, Q - pix0), sX);
-            },
-            [&](int t, int b) {
-                const int pix0 = t * kTcM;
-                const int np = min(kTcM, Q - pix0);
                 tc_epilogue<BF>(T, b, red);
-                if (threadIdx.x < np) epi(pix0 + threadIdx.x, red[threadIdx.x] * inv);
+                if (threadIdx.x < kTcM) {
+                    const int i = tc_tile_pixel(t, threadIdx.x, J.n_l, J.n_m);
+                    if (i >= 0) epi(i, red[threadIdx.x] * inv);
+                }
                 __syncthreads();
             });
     }
@@ -421,27 +415,51 @@ __device__ void adjoint_full(const JobDev &J, const float2 *U, float2 *A, TcWork
 // LSQR (Paige-Saunders) on the free set: min || b - M_F x ||, with
 // M_F x = vect(sum_j s_j x_j c_j c_j^H) and (M_F^H u)_j = s_j Re(c_j^H U c_j).
 // b is in J.W0 on entry.  The bidiagonalisation follows eq. initbeta ..
-// eq. lanczos; rotations and stopping tests as in the FP64 oracle, scalars
-// in FP64.  Returns the iteration count; the solution is in J.xs[0..f).
+// eq. lanczos; rotations and stopping tests as in the FP64 oracle, scalars in
+// FP64.  The u-space vector is kept unnormalised: W0 holds t with u = t * us
+// (us = 1/beta), which saves a normalisation pass per iteration.  Returns the
+// iteration count; the solution is in J.xs[0..f).
 template <int MODE>
 __device__ int lsqr_cta(const JobDev &J, int f, float2 *A, TcWork &T, SolveShared &S, DevInfo &info) {
+    constexpr bool BF = MODE == 2;
     const int p = J.p, pp = p * p;
-    float2 *u = J.W0;
+    const int *fpos = J.fpos;
+    // free-set tiles resident in shared memory for the whole solve (tensor
+    // cores, Kp = 64, at most two 128-pixel tiles)
+    bool resident = false;
+    float sXr = 1.f;
+    unsigned char *stage = nullptr;
+    if constexpr (MODE != 0) {
+        resident = T.Kp == 64 && f <= 2 * kTcM;
+        if (resident) {
+            stage = T.Blo + (T.Blo - T.Bhi);
+            sXr = list_scale(J, fpos, f, S.dbuf);
+            tc_gen_X_cache<BF>(J, T, 0, fpos, 0, min(kTcM, f), sXr);
+            if (f > kTcM) tc_gen_X_cache<BF>(J, T, 1, fpos, kTcM, f - kTcM, sXr);
+        }
+    }
+    for (int j = threadIdx.x; j < f; j += blockDim.x) J.sF[j] = J.scale[J.supp[fpos[j]]];
+    float2 *t = J.W0;
     double acc = 0.0;
-    for (int e = threadIdx.x; e < pp; e += blockDim.x) acc += (double)u[e].x * u[e].x + (double)u[e].y * u[e].y;
+    for (int e = threadIdx.x; e < pp; e += blockDim.x) acc += (double)t[e].x * t[e].x + (double)t[e].y * t[e].y;
     double beta = sqrt(block_sum(acc, S.dbuf));
     const double bnorm = beta;
     for (int j = threadIdx.x; j < f; j += blockDim.x) J.xs[j] = 0.f;
     if (beta == 0.0) { __syncthreads(); return 0; }
+    double us = 1.0 / beta;
+    auto adjoint = [&](auto epi) {
+        if constexpr (MODE != 0) {
+            if (resident) {
+                tc_adjoint_resident<BF>(T, t, p, f, sXr, S.red, S.dbuf, epi);
+                return;
+            }
+        }
+        adjoint_list<MODE>(J, t, fpos, f, A, T, S.red, S.dbuf, epi);
+    };
     {
-        const float ib = (float)(1.0 / beta);
-        for (int e = threadIdx.x; e < pp; e += blockDim.x) u[e] = make_float2(u[e].x * ib, u[e].y * ib);
+        const float fus = (float)us;
+        adjoint([&](int j, float y) { J.v[j] = J.sF[j] * (y * fus); });
     }
-    __syncthreads();
-    const int *fpos = J.fpos;
-    adjoint_list<MODE>(J, u, fpos, f, A, T, S.red, S.dbuf, [&](int j, float t) {
-        J.v[j] = J.scale[J.supp[fpos[j]]] * t;
-    });
     acc = 0.0;
     for (int j = threadIdx.x; j < f; j += blockDim.x) acc += (double)J.v[j] * J.v[j];
     double alpha = sqrt(block_sum(acc, S.dbuf));
@@ -459,33 +477,44 @@ __device__ int lsqr_cta(const JobDev &J, int f, float2 *A, TcWork &T, SolveShare
     int it = 0;
     float *wt = J.xs + J.cap;   // weight scratch (cap floats after xs)
     for (it = 1; it <= maxit; ++it) {
-        // u <- M v - alpha u
-        for (int j = threadIdx.x; j < f; j += blockDim.x) wt[j] = J.scale[J.supp[fpos[j]]] * J.v[j];
+        // t <- M v - alpha u  (u = t * us), beta = ||t||
+        for (int j = threadIdx.x; j < f; j += blockDim.x) wt[j] = J.sF[j] * J.v[j];
         __syncthreads();
         long long tc0 = clock64();
-        forward_cache<MODE>(J, T, fpos, wt, f, nullptr, false, J.W1, A, S.wsm, S.dbuf);
-        info.cyc_lsqr_fwd += (double)(clock64() - tc0);
+        const float fa = (float)(alpha * us);
         acc = 0.0;
-        const float fa = (float)alpha;
-        for (int e = threadIdx.x; e < pp; e += blockDim.x) {
-            const float2 mv = J.W1[e];
-            const float2 t = make_float2(mv.x - fa * u[e].x, mv.y - fa * u[e].y);
-            u[e] = t;
-            acc += (double)t.x * t.x + (double)t.y * t.y;
+        bool done = false;
+        if constexpr (MODE != 0) {
+            if (resident) {
+                float inv;
+                const float *G = tc_forward_resident<BF>(T, stage, f, wt, sXr, &inv, S.dbuf);
+                for (int e = threadIdx.x; e < pp; e += blockDim.x) {
+                    const int bcol = e / p, a = e - bcol * p;
+                    float2 kv = G ? tc_k_entry(G, T.Kp, a, bcol) : make_float2(0.f, 0.f);
+                    const float2 tn = make_float2(kv.x * inv - fa * t[e].x, kv.y * inv - fa * t[e].y);
+                    t[e] = tn;
+                    acc += (double)tn.x * tn.x + (double)tn.y * tn.y;
+                }
+                done = true;
+            }
         }
+        if (!done) {
+            forward_cache<MODE>(J, T, fpos, wt, f, nullptr, false, J.W1, A, S.wsm, S.dbuf);
+            for (int e = threadIdx.x; e < pp; e += blockDim.x) {
+                const float2 mv = J.W1[e];
+                const float2 tn = make_float2(mv.x - fa * t[e].x, mv.y - fa * t[e].y);
+                t[e] = tn;
+                acc += (double)tn.x * tn.x + (double)tn.y * tn.y;
+            }
+        }
+        info.cyc_lsqr_fwd += (double)(clock64() - tc0);
         beta = sqrt(block_sum(acc, S.dbuf));
-        if (beta > 0.0) {
-            const float ib = (float)(1.0 / beta);
-            for (int e = threadIdx.x; e < pp; e += blockDim.x) u[e] = make_float2(u[e].x * ib, u[e].y * ib);
-        }
-        __syncthreads();
+        us = beta > 0.0 ? 1.0 / beta : 0.0;
         anorm2 += alpha * alpha + beta * beta;
         // v <- M^H u - beta v
-        const float fb = (float)beta;
+        const float fb = (float)beta, fus = (float)us;
         tc0 = clock64();
-        adjoint_list<MODE>(J, u, fpos, f, A, T, S.red, S.dbuf, [&](int j, float t) {
-            J.v[j] = J.scale[J.supp[fpos[j]]] * t - fb * J.v[j];
-        });
+        adjoint([&](int j, float y) { J.v[j] = J.sF[j] * (y * fus) - fb * J.v[j]; });
         info.cyc_lsqr_adj += (double)(clock64() - tc0);
         acc = 0.0;
         for (int j = threadIdx.x; j < f; j += blockDim.x) acc += (double)J.v[j] * J.v[j];
@@ -852,7 +881,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_psi_partial_tc(const JobDev *Jp
     const int n = max(0, min(per, J.Q - i0));
     const float sX = steer_scale(J.p);
     tc_forward<BF>(T, J.p, n, wx + i0, sX,
-                   [&](int t, int np) { tc_gen_X_steer<BF>(J, T, 0, i0 + t * kTcM, np, sX); },
+                   [&](int t, int np) { tc_gen_X_range<BF>(J, T, 0, i0 + t * kTcM, np, sX); },
                    nullptr, false, part + (size_t)blockIdx.x * J.p * J.p, dbuf);
     tc_teardown(T, J.p);
 }
@@ -907,7 +936,8 @@ __global__ void k_d2f(const double *src, float *dst, int n) {
 // ---------------------------------------------------------------- launchers
 size_t solve_smem_bytes(int p, int mode) {
     size_t b = (size_t)p * kTile * sizeof(float2);
-    if (mode != 0) b = b > tc_smem_bytes(p) ? b : tc_smem_bytes(p);
+    const size_t tc = tc_smem_bytes(p) + tc_stage_bytes(p);
+    if (mode != 0) b = b > tc ? b : tc;
     return b + 1024;
 }
 size_t bounds_smem_bytes(int p) {

@@ -218,18 +218,42 @@ __device__ inline void tc_teardown(TcWork &T, int p) {
 
 // B = real embedding of U, scaled by a power of two to max |entry| <= 1,
 // split into hi/lo 16-bit tiles.  Row n of B^T (N index) holds, for
-// n < p: [Re U(n,:), -Im U(n,:)], for Kp <= n < Kp+p: [Im U(n,:), Re U(n,:)].
-// Re(a^H U a) = Re(a^H U^H a), so rows are read from columns of U (contiguous)
-// as conj(U(:, n)).  Returns the scale.
+// n < p: [Re V(n,:), -Im V(n,:)], for Kp <= n < Kp+p: [Im V(n,:), Re V(n,:)]
+// with V = U^H; Re(a^H U a) = Re(a^H U^H a), and row n of V is the conjugate
+// of column n of U, which is contiguous.  One pass: each thread keeps its
+// column chunks of U in registers while the CTA finds the scale.
 template <bool BF16>
 __device__ float tc_build_B(const float2 *U, int p, TcWork &T, double *sbuf) {
-    const int Kp = T.Kp, N = 2 * Kp;
+    const int Kp = T.Kp, N = 2 * Kp, nc8 = Kp / 8;
+    constexpr int kMaxItems = 4;          // (Kp/8) * Kp / kThreads <= 4 for Kp <= 128
+    const int items = Kp * nc8;           // (row n < Kp, chunk of 8 columns)
+    float2 v[kMaxItems][8];
     float mx = 0.f;
-    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
-        const float2 u = U[e];
-        mx = fmaxf(mx, fmaxf(fabsf(u.x), fabsf(u.y)));
+#pragma unroll
+    for (int q = 0; q < kMaxItems; ++q) {
+        const int it = threadIdx.x + q * kThreads;
+        const int n = it / nc8, c8 = it - n * nc8;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[q][e] = make_float2(0.f, 0.f);
+        if (it < items && n < p) {
+            const int k0 = c8 * 8;
+            const float2 *src = U + (size_t)n * p + k0;      // U(k0.., n) = conj(V(n, k0..))
+            if ((p & 1) == 0 && k0 + 8 <= p) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float4 x = reinterpret_cast<const float4 *>(src)[e];
+                    v[q][2 * e] = make_float2(x.x, x.y);
+                    v[q][2 * e + 1] = make_float2(x.z, x.w);
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e)
+                    if (k0 + e < p) v[q][e] = src[e];
+            }
+#pragma unroll
+            for (int e = 0; e < 8; ++e) mx = fmaxf(mx, fmaxf(fabsf(v[q][e].x), fabsf(v[q][e].y)));
+        }
     }
-    // max over the CTA
     for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) sbuf[threadIdx.x >> 5] = mx;
     __syncthreads();
@@ -237,33 +261,33 @@ __device__ float tc_build_B(const float2 *U, int p, TcWork &T, double *sbuf) {
     for (int w = 0; w < kThreads / 32; ++w) mx = fmaxf(mx, (float)sbuf[w]);
     __syncthreads();
     const float sc = mx > 0.f ? exp2f(-ceilf(log2f(mx))) : 1.f;
-    const int cpr = N / 8;                   // 16-byte chunks per row
-    for (int it = threadIdx.x; it < N * cpr; it += blockDim.x) {
-        const int n = it / cpr, c = it - n * cpr;
-        const int k0 = c * 8;                // K index of the chunk
-        float v[8];
-        const bool nre = n < Kp;
-        const int row = nre ? n : n - Kp;    // row of U
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int k = k0 + q;
-            const bool kre = k < Kp;
-            const int col = kre ? k : k - Kp;
-            float val = 0.f;
-            if (row < p && col < p) {
-                const float2 u = U[(size_t)row * p + col];   // U(col,row) = conj(U(row,col))
-                // B^T[n][k]: (re,re) Re U, (re,im) -Im U, (im,re) Im U, (im,im) Re U
-                // with U(row,col) = conj(u): Re U = u.x, Im U = -u.y
-                if (nre && kre) val = u.x;
-                else if (nre && !kre) val = u.y;
-                else if (!nre && kre) val = -u.y;
-                else val = u.x;
-            }
-            v[q] = val * sc;
+    for (int q = 0; q < kMaxItems; ++q) {
+        const int it = threadIdx.x + q * kThreads;
+        if (it >= items) break;
+        const int n = it / nc8, c8 = it - n * nc8;
+        // u = U(k, n) = conj(V(n, k)):  Re V = u.x, Im V = -u.y
+        float re[8], nim[8], im[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            re[e] = v[q][e].x * sc;
+            im[e] = -v[q][e].y * sc;
+            nim[e] = v[q][e].y * sc;
         }
         uint4 hi, lo;
-        split8<BF16>(v, hi, lo);
-        const uint32_t off = sw128_off(n, c, N);
+        split8<BF16>(re, hi, lo);                       // (re row, re col): Re V
+        uint32_t off = sw128_off(n, c8, N);
+        *reinterpret_cast<uint4 *>(T.Bhi + off) = hi;
+        *reinterpret_cast<uint4 *>(T.Blo + off) = lo;
+        off = sw128_off(Kp + n, nc8 + c8, N);           // (im row, im col): Re V
+        *reinterpret_cast<uint4 *>(T.Bhi + off) = hi;
+        *reinterpret_cast<uint4 *>(T.Blo + off) = lo;
+        split8<BF16>(nim, hi, lo);                      // (re row, im col): -Im V
+        off = sw128_off(n, nc8 + c8, N);
+        *reinterpret_cast<uint4 *>(T.Bhi + off) = hi;
+        *reinterpret_cast<uint4 *>(T.Blo + off) = lo;
+        split8<BF16>(im, hi, lo);                       // (im row, re col): Im V
+        off = sw128_off(Kp + n, c8, N);
         *reinterpret_cast<uint4 *>(T.Bhi + off) = hi;
         *reinterpret_cast<uint4 *>(T.Blo + off) = lo;
     }
@@ -318,8 +342,26 @@ namespace img {
 
 // X tile (128 rows) from steering vectors of pixels pix0 .. pix0+np-1; rows
 // beyond np are zero.  Values scaled by sX (a power of two).
+// Pixel tiles are 8 (l) x 16 (m) blocks of the grid, so one tile reads only
+// 8 + 16 rows of the separable steering tables (L1-resident) instead of 128.
+constexpr int kTileL = 8, kTileM = 16;
+
+__host__ __device__ inline int tc_num_tiles(int n_l, int n_m) {
+    return ((n_l + kTileL - 1) / kTileL) * ((n_m + kTileM - 1) / kTileM);
+}
+
+// Pixel index of row r of 2-D tile t, or -1 outside the grid.
+__device__ __forceinline__ int tc_tile_pixel(int t, int r, int n_l, int n_m) {
+    const int tl = (n_l + kTileL - 1) / kTileL;
+    const int bm = t / tl, bl = t - bm * tl;
+    const int il = bl * kTileL + (r % kTileL), im = bm * kTileM + r / kTileL;
+    return (il < n_l && im < n_m) ? il + n_l * im : -1;
+}
+
+// X tile (128 rows) of steering vectors for the pixels of 2-D tile t
+// (rows outside the grid are zero), scaled by sX (a power of two).
 template <bool BF16>
-__device__ inline void tc_gen_X_steer(const JobDev &J, TcWork &T, int b, int pix0, int np, float sX) {
+__device__ inline void tc_gen_X_steer(const JobDev &J, TcWork &T, int b, int t, float sX) {
     const int p = J.p, Kp = T.Kp, nc8 = Kp / 8, nl = J.n_l;
     const float2 *__restrict__ El = J.El;
     const float2 *__restrict__ Em = J.Em;
@@ -329,8 +371,8 @@ __device__ inline void tc_gen_X_steer(const JobDev &J, TcWork &T, int b, int pix
         const int r = it / nc8, c8 = it - r * nc8;
         float re[8], im[8];
         const int k0 = c8 * 8;
-        if (r < np && k0 < p) {
-            const int i = pix0 + r;
+        const int i = tc_tile_pixel(t, r, nl, J.n_m);
+        if (i >= 0 && k0 < p) {
             const int mm = i / nl, ll = i - mm * nl;
             if (vec) {
                 const float4 *e = reinterpret_cast<const float4 *>(El + (size_t)ll * p + k0);
@@ -358,6 +400,37 @@ __device__ inline void tc_gen_X_steer(const JobDev &J, TcWork &T, int b, int pix
         } else {
 #pragma unroll
             for (int q = 0; q < 8; ++q) re[q] = im[q] = 0.f;
+        }
+        uint4 hi, lo;
+        split8<BF16>(re, hi, lo);
+        uint32_t off = sw128_off(r, c8, kTcM);
+        *reinterpret_cast<uint4 *>(xh + off) = hi;
+        *reinterpret_cast<uint4 *>(xl + off) = lo;
+        split8<BF16>(im, hi, lo);
+        off = sw128_off(r, nc8 + c8, kTcM);
+        *reinterpret_cast<uint4 *>(xh + off) = hi;
+        *reinterpret_cast<uint4 *>(xl + off) = lo;
+    }
+}
+
+// X tile of the consecutive pixels pix0 .. pix0+np-1 (forward over all
+// pixels, where every pixel's weight comes from a linear array).
+template <bool BF16>
+__device__ inline void tc_gen_X_range(const JobDev &J, TcWork &T, int b, int pix0, int np, float sX) {
+    const int p = J.p, Kp = T.Kp, nc8 = Kp / 8, nl = J.n_l;
+    unsigned char *xh = T.Xhi[b], *xl = T.Xlo[b];
+    for (int it = threadIdx.x; it < kTcM * nc8; it += blockDim.x) {
+        const int r = it / nc8, c8 = it - r * nc8;
+        float re[8], im[8];
+        const int i = pix0 + r;
+        const int mm = i / nl, ll = i - mm * nl;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int k = c8 * 8 + q;
+            float2 a = make_float2(0.f, 0.f);
+            if (r < np && k < p) a = steer(J, ll, mm, k);
+            re[q] = a.x * sX;
+            im[q] = a.y * sX;
         }
         uint4 hi, lo;
         split8<BF16>(re, hi, lo);
@@ -553,12 +626,11 @@ __device__ inline void tc_issue_fwd(const TcWork &T, uint32_t idesc, bool first)
 // Read the forward accumulator into shared memory G (2Kp x 2Kp FP32, row m
 // at stride 2Kp + 1 against bank conflicts), reusing the operand buffers.
 // All threads.
-__device__ inline float *tc_read_fwd(const TcWork &T) {
+__device__ inline float *tc_read_fwd(const TcWork &T, float *G) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int half = warp >> 2, m = 32 * (warp & 3) + lane;
     const int N = 2 * T.Kp;
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-    float *G = reinterpret_cast<float *>(T.Xhi[0]);
     for (int c0 = 0; c0 < T.Kp; c0 += 16) {
         float d[16];
         tmem_ld16(T.tmem + lane_base + (uint32_t)(2 * N + half * T.Kp + c0), d);
@@ -587,6 +659,15 @@ __device__ inline float pow2_scale_of(const float *w, int n, double *sbuf) {
 
 namespace img {
 
+__device__ inline void tc_combine_fwd(const TcWork &T, int p, const float *G, float inv,
+                                      const float2 *base, bool base_identity, float2 *K);
+
+// K(a, b) from the forward Gram matrix G (row stride 2Kp + 1), unscaled.
+__device__ __forceinline__ float2 tc_k_entry(const float *G, int Kp, int a, int b) {
+    const int ld = 2 * Kp + 1;
+    return make_float2(G[a * ld + b] + G[(Kp + a) * ld + Kp + b], G[(Kp + a) * ld + b] - G[a * ld + Kp + b]);
+}
+
 // Forward driver: K = base + sum_j wt[j] c_j c_j^H over n list entries whose
 // unweighted pixel-major tiles gen0(t, np) writes into buffer 0 (scaled by
 // sX).  Needs Kp = 64 (M = N = 128).  K: p x p complex, global memory.
@@ -610,8 +691,14 @@ __device__ void tc_forward(TcWork &T, int p, int n, const float *wt, float sX, G
         tc_fence_after();
         __syncthreads();
     }
-    const float *G = ntiles ? tc_read_fwd(T) : nullptr;
-    const float inv = 1.f / (sX * sX * sW);
+    const float *G = ntiles ? tc_read_fwd(T, reinterpret_cast<float *>(T.Xhi[0])) : nullptr;
+    tc_combine_fwd(T, p, G, 1.f / (sX * sX * sW), base, base_identity, K);
+}
+
+// K = base + (G -> complex p x p), scaled by inv; G may be null (empty sum).
+__device__ inline void tc_combine_fwd(const TcWork &T, int p, const float *G, float inv,
+                                      const float2 *base, bool base_identity, float2 *K) {
+    const int N = 2 * T.Kp;
     const int ld = N + 1, Kp = T.Kp;
     for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
         const int bcol = e / p, a = e - bcol * p;
@@ -626,6 +713,144 @@ __device__ void tc_forward(TcWork &T, int p, int n, const float *wt, float sX, G
         K[e] = make_float2(bb.x + kr, bb.y + ki);
     }
     __syncthreads();
+}
+
+}  // namespace img
+
+namespace img {
+
+// ---------------------------------------------------------------- resident LSQR
+// During one LSQR solve the free set is fixed, so (for f <= 256 and Kp = 64)
+// its X tiles stay in shared memory for every iteration: tile 0 in buffer 0,
+// tile 1 in buffer 1.  The forward product stages only the weighted K-chunks
+// (32 pixels, both MN blocks) in a 16 KB region after the B tiles.
+constexpr int kChunk = 16;              // pixels per forward K-chunk (one MMA K-step)
+
+// Two staging buffers (hi + lo, MN blocks x 16 rows x 128 bytes each).
+__host__ __device__ inline size_t tc_stage_bytes(int p) {
+    const int Kp = (p + 31) / 32 * 32;
+    return (size_t)2 * 2 * (2 * Kp / 64) * kChunk * 128;
+}
+
+// Weighted chunk rows r0 .. r0+31 of resident tile `tile` into the staging
+// region (MN blocks of 32 rows x 128 bytes), rows j >= nrow zero.
+template <bool BF16>
+__device__ inline void tc_weight_chunk(TcWork &T, unsigned char *stage, int tile, int r0, int nrow,
+                                       const float *w, float sW) {
+    const int nch = 2 * T.Kp / 8;
+    const size_t half_bytes = (size_t)(2 * T.Kp / 64) * kChunk * 128;
+    for (int it = threadIdx.x; it < kChunk * nch; it += blockDim.x) {
+        const int rr = it / nch, c = it - rr * nch;
+        const uint32_t src = sw128_off(r0 + rr, c, kTcM);
+        const uint32_t dst = sw128_off(rr, c, kChunk);
+        const float wr = rr < nrow ? sW * w[rr] : 0.f;
+        const uint4 h4 = *reinterpret_cast<const uint4 *>(T.Xhi[tile] + src);
+        const uint4 l4 = *reinterpret_cast<const uint4 *>(T.Xlo[tile] + src);
+        const uint32_t hw[4] = {h4.x, h4.y, h4.z, h4.w}, lw[4] = {l4.x, l4.y, l4.z, l4.w};
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float h0, h1, l0, l1;
+            if (BF16) {
+                h0 = __uint_as_float(hw[q] << 16);
+                h1 = __uint_as_float(hw[q] & 0xffff0000u);
+                l0 = __uint_as_float(lw[q] << 16);
+                l1 = __uint_as_float(lw[q] & 0xffff0000u);
+            } else {
+                h0 = __half2float(__ushort_as_half((unsigned short)(hw[q] & 0xffffu)));
+                h1 = __half2float(__ushort_as_half((unsigned short)(hw[q] >> 16)));
+                l0 = __half2float(__ushort_as_half((unsigned short)(lw[q] & 0xffffu)));
+                l1 = __half2float(__ushort_as_half((unsigned short)(lw[q] >> 16)));
+            }
+            v[2 * q] = wr * (h0 + l0);
+            v[2 * q + 1] = wr * (h1 + l1);
+        }
+        uint4 hi, lo;
+        split8<BF16>(v, hi, lo);
+        *reinterpret_cast<uint4 *>(stage + dst) = hi;
+        *reinterpret_cast<uint4 *>(stage + half_bytes + dst) = lo;
+    }
+}
+
+// MMAs of one staged chunk against resident rows r0 .. r0+31 of `tile`,
+// accumulating into the forward accumulator; commits to barrier 0.
+__device__ inline void tc_issue_fwd_chunk(const TcWork &T, const unsigned char *stage, int tile, int r0,
+                                          uint32_t idesc, bool first, int bar) {
+    const int N = 2 * T.Kp;
+    tc_fence_after();
+    const size_t half_bytes = (size_t)(N / 64) * kChunk * 128;
+    const uint32_t ah = smem_u32(stage), al = smem_u32(stage + half_bytes);
+    const uint32_t bh = smem_u32(T.Xhi[tile]), bl = smem_u32(T.Xlo[tile]);
+    const uint32_t d = T.tmem + (uint32_t)(2 * N);
+    for (int s = 0; s < kChunk / 16; ++s) {
+        const uint32_t ao = s * 2048, bo = (uint32_t)((r0 + 16 * s) / 8) * 1024;
+        const uint32_t alb = kChunk * 128, blb = kTcM * 128;
+        mma_f16(d, sw128_desc_mn(ah + ao, alb, 1024), sw128_desc_mn(bh + bo, blb, 1024), idesc,
+                (first && s == 0) ? 0u : 1u);
+        mma_f16(d, sw128_desc_mn(ah + ao, alb, 1024), sw128_desc_mn(bl + bo, blb, 1024), idesc, 1u);
+        mma_f16(d, sw128_desc_mn(al + ao, alb, 1024), sw128_desc_mn(bh + bo, blb, 1024), idesc, 1u);
+    }
+    mma_commit(&T.bar[bar]);
+}
+
+// Forward over the resident free-set tiles: G = sum_j w_j x_j x_j^T read out
+// into the B + staging region (the B tile is rebuilt later).  Weighted
+// 16-pixel chunks alternate between two staging buffers, so weighting chunk
+// c+1 overlaps the MMAs of chunk c; a buffer is reused only after the MMAs
+// that read it completed.  Returns G (scaled by sX^2 sW; *scale = 1/that).
+template <bool BF16>
+__device__ const float *tc_forward_resident(TcWork &T, unsigned char *stage, int f, const float *w,
+                                            float sX, float *scale, double *dbuf) {
+    const float sW = pow2_scale_of(w, f, dbuf);
+    const uint32_t idesc = idesc_f16_mn(2 * T.Kp, BF16 ? 1 : 0);
+    const int nchunks = (f + kChunk - 1) / kChunk;
+    const size_t buf = (size_t)2 * (2 * T.Kp / 64) * kChunk * 128;   // one staging buffer (hi + lo)
+    for (int c = 0; c < nchunks; ++c) {
+        const int b = c & 1;
+        if (c >= 2) {
+            if (!mbar_wait(&T.bar[b], T.phase[b])) T.timeouts++;
+            T.phase[b] ^= 1u;
+            tc_fence_after();
+        }
+        const int j0 = c * kChunk, tile = j0 / kTcM, r0 = j0 % kTcM;
+        tc_weight_chunk<BF16>(T, stage + b * buf, tile, r0, min(kChunk, f - j0), w + j0, sW);
+        fence_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) tc_issue_fwd_chunk(T, stage + b * buf, tile, r0, idesc, c == 0, b);
+    }
+    for (int c = max(0, nchunks - 2); c < nchunks; ++c) {
+        const int b = c & 1;
+        if (!mbar_wait(&T.bar[b], T.phase[b])) T.timeouts++;
+        T.phase[b] ^= 1u;
+    }
+    tc_fence_after();
+    __syncthreads();
+    *scale = 1.f / (sX * sX * sW);
+    return nchunks ? tc_read_fwd(T, reinterpret_cast<float *>(T.Bhi)) : nullptr;
+}
+
+// Adjoint over the resident tiles: epi(j, Re(c_j^H U c_j)) for j < f.
+template <bool BF16, class Epi>
+__device__ void tc_adjoint_resident(TcWork &T, const float2 *U, int p, int f, float sX, float *red,
+                                    double *dbuf, Epi epi) {
+    const float sB = tc_build_B<BF16>(U, p, T, dbuf);
+    const uint32_t idesc = idesc_f16(2 * T.Kp, BF16 ? 1 : 0);
+    const int ntiles = (f + kTcM - 1) / kTcM;
+    fence_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int t = 0; t < ntiles; ++t) tc_issue(T, t, idesc);
+    const float inv = 1.f / (sX * sX * sB);
+    for (int t = 0; t < ntiles; ++t) {
+        if (!mbar_wait(&T.bar[t], T.phase[t])) T.timeouts++;
+        T.phase[t] ^= 1u;
+        tc_fence_after();
+        __syncthreads();
+        tc_epilogue<BF16>(T, t, red);
+        const int j = t * kTcM + threadIdx.x;
+        if (threadIdx.x < kTcM && j < f) epi(j, red[threadIdx.x] * inv);
+        __syncthreads();
+    }
 }
 
 }  // namespace img
