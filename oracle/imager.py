@@ -421,3 +421,132 @@ def image(ant_xyz, l, m, lam, R, N, prm: Params) -> ImageResult:
 
 def image_job(job, prm: Params) -> ImageResult:
     return image(job.ant_xyz, job.l, job.m, job.lam, job.R, job.N, prm)
+
+
+# ---------------------------------------------------------------- replay
+@dataclass
+class FollowReport:
+    """Outcome of replaying a decision log through the oracle."""
+    result: SolveResult
+    decisions: int = 0
+    ties: int = 0                 # decisions that differ from the oracle's own choice
+    violations: list = field(default_factory=list)
+    max_margin: float = 0.0       # largest tie margin seen (relative)
+
+
+def active_set_follow(prob: CostProblem, eps: np.ndarray, prm: Params, log, tol: float = 1e-4
+                      ) -> FollowReport:
+    """Run Table I (as active_set) but take every discrete decision from `log`
+    [(kind, pixel), ...] (kind 0 free, 1 clamp to L, 2 clamp to U; an empty
+    remainder means the logged run stopped).  Each logged decision is checked
+    against the oracle's own arithmetic: it must be the oracle's choice, or a
+    tie within `tol` relative to the quantity's scale:
+      free    lambda_j < -eps_j and lambda_j <= lambda_min, within tol * scale
+              (scale: largest |gradient| at sigma = 0, the dirty image peak);
+      stop    no lambda_i + eps_i below -tol * scale;
+      feasible / clamp   z inside / outside its bounds unless within tol of one;
+      clamp pixel   mu_j <= mu_max (1 + tol) with the direction's sign.
+    Test infrastructure for path-dependent results (kappa > 0): when all
+    decisions are admissible, the logged run followed a valid path of the
+    method and its image must match the oracle's image along that path."""
+    M, b, up = prob.M, prob.b, prob.upper
+    Q = M.shape[1]
+    x = np.zeros(Q)
+    sets = np.full(Q, SET_L, dtype=np.int8)
+    rep = FollowReport(result=None)
+    scale = float(np.max(np.abs(gradient(prob, np.zeros(Q)))))
+    k = 0
+    flag = True
+    outer = 0
+    lsqr_total = 0
+    converged = False
+    g = None
+    free_next = -1
+    max_outer = prm.max_outer if prm.max_outer > 0 else 10 * Q + 100
+    tau = prm.feas_tol
+    while outer < max_outer:
+        outer += 1
+        if flag:
+            F = np.nonzero(sets == SET_F)[0]
+            U = np.nonzero(sets == SET_U)[0]
+            if F.size:
+                b_sub = b - M[:, U] @ x[U]
+                maxit = prm.lsqr_maxit if prm.lsqr_maxit > 0 else 4 * F.size + 20
+                res = lsqr(M[:, F], b_sub, prm.lsqr_atol, prm.lsqr_btol, maxit)
+                lsqr_total += res.iters
+                z = res.x
+            else:
+                z = np.zeros(0)
+            uF = up[F]
+            viol = np.maximum(-z / uF - tau, z / uF - (1.0 + tau)) if F.size else np.zeros(0)
+            feas_o = not np.any(viol > 0)
+            nxt = log[k] if k < len(log) else None
+            feas_l = not (nxt is not None and nxt[0] in (1, 2))
+            rep.decisions += 1
+            if feas_o != feas_l:
+                margin = float(np.max(np.abs(viol))) if viol.size else 0.0
+                rep.max_margin = max(rep.max_margin, margin)
+                if margin > tol:
+                    rep.violations.append(("feasibility", k, margin))
+                rep.ties += 1
+            if feas_l:
+                x[F] = np.clip(z, 0.0, uF)
+                flag = False
+                g = gradient(prob, x)
+                lam = np.where(sets == SET_U, -g, g)
+                act = sets != SET_F
+                slack = np.where(act, lam + eps, np.inf)
+                rep.decisions += 1
+                if nxt is None:
+                    worst = float(np.min(slack))
+                    if worst < -tol * scale:
+                        rep.violations.append(("stop", k, worst / scale))
+                    converged = True
+                    break
+                j = int(nxt[1])
+                if nxt[0] != 0 or not act[j]:
+                    rep.violations.append(("free-kind", k, float("nan")))
+                    break
+                lam_min = float(np.min(np.where(act & (slack < 0), lam, np.inf)))
+                margin = max((lam[j] - lam_min) / scale, slack[j] / scale)
+                if np.argmin(np.where(act & (slack < 0), lam, np.inf)) != j:
+                    rep.ties += 1
+                    rep.max_margin = max(rep.max_margin, margin)
+                if margin > tol:
+                    rep.violations.append(("free", k, margin))
+                free_next = j
+                k += 1
+            else:
+                i = int(nxt[1])
+                pos = np.nonzero(F == i)[0]
+                if pos.size != 1:
+                    rep.violations.append(("clamp-not-free", k, float("nan")))
+                    break
+                q = int(pos[0])
+                pdir = z - x[F]
+                mu = np.full(F.size, np.inf)
+                pp, pn = pdir > 0, pdir < 0
+                mu[pp] = (uF[pp] - x[F][pp]) / pdir[pp]
+                mu[pn] = -x[F][pn] / pdir[pn]
+                mu_max = float(np.min(mu))
+                rep.decisions += 1
+                if (nxt[0] == 2) != (pdir[q] > 0) or mu[q] > mu_max * (1 + tol) + 1e-300:
+                    if F[int(np.argmin(mu))] != i:
+                        rep.violations.append(("clamp", k, float(mu[q] / max(mu_max, 1e-300) - 1)))
+                if F[int(np.argmin(mu))] != i:
+                    rep.ties += 1
+                step = float(mu[q])
+                x[F] = x[F] + step * pdir
+                if nxt[0] == 2:
+                    sets[i] = SET_U
+                    x[i] = up[i]
+                else:
+                    sets[i] = SET_L
+                    x[i] = 0.0
+                k += 1
+                flag = True
+        else:
+            sets[free_next] = SET_F
+            flag = True
+    rep.result = SolveResult(prob.to_sigma * x, x, sets, outer, lsqr_total, converged, [], g)
+    return rep
