@@ -88,9 +88,26 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- workload
-def make_jobs(B: int, seed0: int):
+def rank_seeds(rank: int, B: int):
+    """Seeds of the B images rank `rank` solves: disjoint across ranks (the
+    images are independent, so ranks are replicas on different data)."""
+    return [2000 + 100_000 * rank + j for j in range(B)]
+
+
+def make_jobs(seeds):
     import synth
-    return [synth.mid(seed=seed0 + j) for j in range(B)]
+    return [synth.mid(seed=s) for s in seeds]
+
+
+def reduce_max(value: float, device=None) -> float:
+    """Max over ranks (the job is as slow as its slowest rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def sm_count() -> int:
@@ -122,7 +139,7 @@ def run_ours(args, rank: int, world: int):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     B = args.batch or 2 * sm_count()
-    jobs = make_jobs(B, 2000 + 100_000 * rank)
+    jobs = make_jobs(rank_seeds(rank, B))
     stream = torch.cuda.Stream(device=dev)
     prec = PRECISIONS[args.precision]
     ims = [G.Imager(j.ant_xyz, j.l, j.m, j.lam, stream=stream.cuda_stream, precision=prec)
@@ -166,11 +183,7 @@ def run_ours(args, rank: int, world: int):
     t_step = [e0.elapsed_time(e2) / 1e3 for e0, _, e2 in ev]
     t_prep = [e0.elapsed_time(e1) / 1e3 for e0, e1, _ in ev]
     t_solve = [e1.elapsed_time(e2) / 1e3 for _, e1, e2 in ev]
-    total = sum(t_step)
-    if world > 1:
-        t = torch.tensor([total], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total = float(t.item())
+    total = reduce_max(sum(t_step), dev)
     flops = [sum(i.op_flops for i in infos) for infos in infos_all]
     conv = sum(i.converged for infos in infos_all for i in infos)
     outer = float(np.mean([i.outer for infos in infos_all for i in infos]))
@@ -192,11 +205,7 @@ def run_ours(args, rank: int, world: int):
             G.prepare_batch(ims)
             G.solve_batch(ims, outs=host_out)
         torch.cuda.synchronize()
-        te = (time.perf_counter() - t0) / ke
-        if world > 1:
-            t = torch.tensor([te], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            te = float(t.item())
+        te = reduce_max((time.perf_counter() - t0) / ke, dev)
         e2e = {"value": world * B / te, "unit": METRIC,
                "h2d_bytes_per_step": int(sum(j.R.nbytes for j in jobs)),
                "d2h_bytes_per_step": int(sum(j.Q * 8 for j in jobs)),
