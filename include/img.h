@@ -233,6 +233,38 @@ img_status img_psi_noalloc(int p, int n_l, int n_m, const double *ant_xyz, const
                            const double *m, double lambda, const double *x, double *Kout,
                            void *stream);
 
+/* ---------------------------------------------------------------- serving
+ * Continuous batching of independent jobs (not in the paper; jobs are
+ * independent, Sec. V-B).  A scheduler thread admits submitted jobs while
+ * fewer than max_inflight_jobs are on the GPU and the job contexts fit in
+ * hbm_budget_bytes (contexts of the same p, n_l, n_m are pooled and reused),
+ * and launches each admitted group - factor, bounds, solve - on one of
+ * n_streams streams.  Later groups run beside earlier ones on the device.
+ * A job's result does not depend on what else is in flight. */
+typedef struct img_server img_server;
+typedef struct {
+    size_t hbm_budget_bytes;    /* device memory for pooled job contexts        */
+    int max_inflight_jobs;      /* jobs on the GPU at once (0: 2 x SM count)     */
+    int max_batch;              /* jobs per launch group (0: max_inflight_jobs)  */
+    int n_streams;              /* launch streams (0: 4)                         */
+} img_server_params;
+
+/* Defaults: 8 GiB budget, 0, 0, 4 streams. */
+void img_server_params_default(img_server_params *p);
+img_status img_server_create(const img_server_params *prm, img_server **out);
+/* Queue one job: *prm describes it as for img_create (arrays copied), R and N
+ * as for img_set_covariance (host memory, copied).  *job_id identifies it. */
+img_status img_server_submit(img_server *s, const img_params *prm, const void *R, int dtype,
+                             long long N, long long *job_id);
+/* Wait up to timeout_ms for job_id; on completion copy its image (Q doubles,
+ * host) and report (either may be NULL), set *latency_ms (submit to done,
+ * may be NULL), forget the job and return its solve status.  IMG_ETIMEOUT
+ * when it is still running (call again), IMG_EINVAL for an unknown id. */
+img_status img_server_wait(img_server *s, long long job_id, double *sigma, img_solve_info *info,
+                           double timeout_ms, double *latency_ms);
+/* Finish queued work, stop the scheduler and free everything. */
+void img_server_destroy(img_server *s);
+
 /* Release all device memory of ctx.  NULL is allowed. */
 void img_destroy(img_ctx *ctx);
 

@@ -25,7 +25,8 @@ EXPORTS = ("img_params_default", "img_create", "img_set_covariance", "img_dirty"
            "img_mvdr_bound", "img_solve", "img_get_sets", "img_get_gradient", "img_get_events",
            "img_psi",
            "img_psi_adj", "img_prepare_batch", "img_solve_batch", "img_psi_noalloc",
-           "img_destroy", "img_status_str")
+           "img_server_params_default", "img_server_create", "img_server_submit",
+           "img_server_wait", "img_server_destroy", "img_destroy", "img_status_str")
 
 
 class ImgParams(C.Structure):
@@ -49,6 +50,11 @@ class SolveInfo(C.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ServerParams(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_inflight_jobs", C.c_int),
+                ("max_batch", C.c_int), ("n_streams", C.c_int)]
 
 
 class ImgError(RuntimeError):
@@ -103,6 +109,16 @@ def load(build_if_missing: bool = False) -> C.CDLL:
     lib.img_solve_batch.restype = i
     lib.img_psi_noalloc.argtypes = [i, i, i, dp, dp, dp, C.c_double, dp, dp, vp]
     lib.img_psi_noalloc.restype = i
+    lib.img_server_params_default.argtypes = [C.POINTER(ServerParams)]
+    lib.img_server_params_default.restype = None
+    lib.img_server_create.argtypes = [C.POINTER(ServerParams), C.POINTER(vp)]
+    lib.img_server_create.restype = i
+    lib.img_server_submit.argtypes = [vp, C.POINTER(ImgParams), dp, i, ll, C.POINTER(ll)]
+    lib.img_server_submit.restype = i
+    lib.img_server_wait.argtypes = [vp, ll, dp, C.POINTER(SolveInfo), C.c_double, C.POINTER(C.c_double)]
+    lib.img_server_wait.restype = i
+    lib.img_server_destroy.argtypes = [vp]
+    lib.img_server_destroy.restype = None
     lib.img_destroy.argtypes = [vp]
     lib.img_destroy.restype = None
     lib.img_status_str.argtypes = [i]
@@ -285,3 +301,66 @@ def solve_batch(imagers, outs=None, allow=(IMG_ENOTCONV,)):
     code = lib.img_solve_batch(hs, n, ps, infos, dev)
     _check(code, "img_solve_batch", allow)
     return outs, list(infos)
+
+
+class Server:
+    """Continuous-batching job server (wraps img_server)."""
+
+    def __init__(self, hbm_budget_bytes=None, max_inflight_jobs=0, max_batch=0, n_streams=0):
+        self._lib = load()
+        sp = ServerParams()
+        self._lib.img_server_params_default(C.byref(sp))
+        if hbm_budget_bytes is not None:
+            sp.hbm_budget_bytes = int(hbm_budget_bytes)
+        sp.max_inflight_jobs = int(max_inflight_jobs)
+        sp.max_batch = int(max_batch)
+        if n_streams:
+            sp.n_streams = int(n_streams)
+        h = C.c_void_p()
+        _check(self._lib.img_server_create(C.byref(sp), C.byref(h)), "img_server_create")
+        self.h = h
+        self._Q = {}
+
+    def submit(self, ant_xyz, l, m, lam, R, N, **kw) -> int:
+        ant = np.ascontiguousarray(ant_xyz, dtype=np.float64)
+        l = np.ascontiguousarray(l, dtype=np.float64)
+        m = np.ascontiguousarray(m, dtype=np.float64)
+        prm = default_params()
+        prm.p, prm.n_l, prm.n_m = ant.shape[0], l.shape[0], m.shape[0]
+        prm.ant_xyz = ant.ctypes.data_as(C.POINTER(C.c_double))
+        prm.l = l.ctypes.data_as(C.POINTER(C.c_double))
+        prm.m = m.ctypes.data_as(C.POINTER(C.c_double))
+        prm.lambda_ = float(lam)
+        for k, v in kw.items():
+            setattr(prm, k, v)
+        Rf = np.asfortranarray(R, dtype=np.complex128)
+        jid = C.c_longlong()
+        _check(self._lib.img_server_submit(self.h, C.byref(prm), Rf.ctypes.data, C128, int(N),
+                                           C.byref(jid)), "img_server_submit")
+        self._Q[jid.value] = prm.n_l * prm.n_m
+        return jid.value
+
+    def submit_job(self, job, **kw) -> int:
+        return self.submit(job.ant_xyz, job.l, job.m, job.lam, job.R, job.N, **kw)
+
+    def wait(self, job_id: int, timeout_ms: float = 600_000.0, allow=(IMG_ENOTCONV,)):
+        """(image, info, latency_ms) of a finished job."""
+        out = np.empty(self._Q[job_id], dtype=np.float64)
+        info = SolveInfo()
+        lat = C.c_double()
+        code = self._lib.img_server_wait(self.h, int(job_id), out.ctypes.data, C.byref(info),
+                                         float(timeout_ms), C.byref(lat))
+        _check(code, "img_server_wait", allow)
+        del self._Q[job_id]
+        return out, info, lat.value
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self._lib.img_server_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

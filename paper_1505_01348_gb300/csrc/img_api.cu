@@ -629,3 +629,407 @@ void img_destroy(img_ctx *c) {
 }
 
 }  // extern "C"
+
+// ============================================================== serving
+// Continuous batching of independent imaging jobs (not in the paper).  A
+// scheduler thread admits queued jobs while in-flight slots and the HBM
+// budget allow, reuses pooled job contexts of the same shape, and launches
+// each admitted group (factor, bounds, solve) on a free stream of a small
+// pool; groups launched later run next to earlier ones on the device, whose
+// block scheduler places the new CTAs as SMs free up.  No kernel waits on the
+// host: completion is an event the scheduler polls.
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <thread>
+#include <tuple>
+#include <unordered_map>
+#include <algorithm>
+
+namespace {
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct SJob {
+    long long id = 0;
+    img_params prm{};
+    std::vector<double> ant, l, m, R;    // geometry and complex128 covariance (interleaved)
+    long long N = 0;
+    double t_submit = 0, t_start = 0, t_done = 0;
+    int state = 0;                       // 0 queued, 1 on the GPU, 2 done
+    img_status st = IMG_OK;
+    std::vector<double> sigma;
+    img_solve_info info{};
+    img_ctx *ctx = nullptr;
+};
+
+struct SSlot {                           // one launch stream and its workspace
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;
+    JobDev **jobs = nullptr;
+    DevInfo *infos = nullptr;
+    int *status = nullptr;
+    DevInfo *h_infos = nullptr;          // pinned
+    std::vector<SJob *> group;
+    bool busy = false;
+};
+
+using ShapeKey = std::tuple<int, int, int, int>;   // p, n_l, n_m, support cap
+
+ShapeKey key_of(const img_params &p) {
+    const int Q = p.n_l * p.n_m;
+    const int cap = p.support_cap > 0 ? std::min(p.support_cap, Q) : std::min(Q, 16384);
+    return ShapeKey(p.p, p.n_l, p.n_m, cap);
+}
+
+// Load a job's parameters, geometry and covariance into a pooled context of
+// the same shape (asynchronous on stream s).
+img_status reconfigure(img_ctx *c, SJob *j, cudaStream_t s) {
+    JobDev &J = c->hj;
+    const img_params &P = j->prm;
+    c->prm = P;
+    c->ant = j->ant;
+    c->l = j->l;
+    c->m = j->m;
+    c->prm.ant_xyz = c->ant.data();
+    c->prm.l = c->l.data();
+    c->prm.m = c->m.data();
+    c->prm.stream = nullptr;
+    J.cost = P.cost;
+    J.bound = P.bound;
+    J.bias_c = P.bias_c ? 1 : 0;
+    J.inflate = P.inflate;
+    J.lsqr_maxit = P.lsqr_maxit;
+    J.max_outer = P.max_outer;
+    J.precision = P.precision;
+    J.alpha = P.alpha;
+    J.kappa = P.kappa;
+    J.eps_floor = P.eps_floor;
+    J.lam = P.lambda;
+    J.lsqr_atol = P.lsqr_atol;
+    J.lsqr_btol = P.lsqr_btol;
+    J.feas_tol = P.feas_tol;
+    J.N = j->N;
+    const int p = P.p;
+    CK(cudaMemcpyAsync((void *)J.ant, c->ant.data(), 3 * p * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync((void *)J.lg, c->l.data(), P.n_l * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync((void *)J.mg, c->m.data(), P.n_m * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(J.R64, j->R.data(), (size_t)p * p * sizeof(double2), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(J.flags, 0xff, sizeof(int), s));
+    CK(cudaMemsetAsync(J.flags + 1, 0, sizeof(int), s));
+    CK(cudaMemcpyAsync(c->dj, &J, sizeof(JobDev), cudaMemcpyHostToDevice, s));
+    CK(img::launch_tables(c->djp, 1, s));
+    c->has_cov = true;
+    c->prepared = false;
+    c->solved = false;
+    return IMG_OK;
+}
+
+}  // namespace
+
+struct img_server {
+    img_server_params prm{};
+    int device = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::thread th;
+    bool stop = false;
+    long long next_id = 0;
+    std::unordered_map<long long, std::unique_ptr<SJob>> jobs;
+    std::deque<SJob *> pending;
+    std::map<ShapeKey, std::vector<img_ctx *>> free_ctx;
+    std::vector<img_ctx *> all_ctx;
+    size_t bytes_used = 0;
+    int inflight = 0;
+    std::vector<SSlot> slots;
+    img_status fatal = IMG_OK;
+
+    img_ctx *acquire(SJob *j) {
+        auto &v = free_ctx[key_of(j->prm)];
+        if (!v.empty()) {
+            img_ctx *c = v.back();
+            v.pop_back();
+            return c;
+        }
+        img_params p = j->prm;
+        p.ant_xyz = j->ant.data();
+        p.l = j->l.data();
+        p.m = j->m.data();
+        p.stream = nullptr;
+        // size check against the budget before allocating
+        img_ctx probe;
+        probe.prm = p;
+        probe.hj.cap = std::get<3>(key_of(p));
+        probe.hj.ev_cap = (int)std::min<long long>(p.max_outer > 0 ? p.max_outer : 10LL * p.n_l * p.n_m + 100,
+                                                  1 << 20);
+        {
+            int sms = 1;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+            const size_t pp8 = (size_t)p.p * p.p * sizeof(float2);
+            probe.nparts = std::max(1, std::min(2 * std::max(1, sms), (int)std::max<size_t>(1, (4u << 20) / pp8)));
+        }
+        const size_t need = carve(&probe, nullptr);
+        if (bytes_used + need > prm.hbm_budget_bytes) return nullptr;
+        img_ctx *c = nullptr;
+        if (img_create(&p, &c) != IMG_OK) return nullptr;
+        bytes_used += c->dbytes;
+        all_ctx.push_back(c);
+        return c;
+    }
+
+    void release(img_ctx *c) { free_ctx[key_of(c->prm)].push_back(c); }
+
+    // Free every pooled (idle) context; only called with nothing in flight.
+    void evict_free() {
+        for (auto &kv : free_ctx) {
+            for (img_ctx *c : kv.second) {
+                bytes_used -= c->dbytes;
+                all_ctx.erase(std::find(all_ctx.begin(), all_ctx.end(), c));
+                img_destroy(c);
+            }
+            kv.second.clear();
+        }
+    }
+
+    img_status launch(SSlot &sl, std::vector<SJob *> &group) {
+        const int n = (int)group.size();
+        std::vector<img_ctx *> ctxs(n);
+        for (int q = 0; q < n; ++q) {
+            ctxs[q] = group[q]->ctx;
+            img_status st = reconfigure(ctxs[q], group[q], sl.s);
+            if (st != IMG_OK) return st;
+            group[q]->t_start = now_ms();
+            group[q]->state = 1;
+        }
+        const Groups g = group_by_mode(ctxs.data(), n);
+        std::vector<JobDev *> ptrs(n);
+        for (int q = 0; q < n; ++q) ptrs[q] = ctxs[g.order[q]]->dj;
+        CK(cudaMemcpyAsync(sl.jobs, ptrs.data(), n * sizeof(JobDev *), cudaMemcpyHostToDevice, sl.s));
+        for (int md = 0; md < 3; ++md) {
+            const int nb = g.end[md] - g.begin[md];
+            if (!nb) continue;
+            JobDev *const *jp = sl.jobs + g.begin[md];
+            CK(img::launch_factor(jp, nb, sl.s));
+            CK(img::launch_bounds(jp, nb, g.max_tiles[md], g.max_p[md], md, sl.s));
+            CK(img::launch_finalize(jp, nb, sl.s, nullptr));
+            CK(img::launch_solve(jp, nb, g.max_p[md], md, sl.infos + g.begin[md], nullptr, sl.s));
+        }
+        CK(cudaMemcpyAsync(sl.h_infos, sl.infos, n * sizeof(DevInfo), cudaMemcpyDeviceToHost, sl.s));
+        CK(cudaEventRecord(sl.ev, sl.s));
+        // results in job order: remember the permutation through group order
+        sl.group.assign(n, nullptr);
+        for (int q = 0; q < n; ++q) sl.group[q] = group[g.order[q]];
+        sl.busy = true;
+        inflight += n;
+        return IMG_OK;
+    }
+
+    void finish(SSlot &sl) {
+        const int n = (int)sl.group.size();
+        for (int q = 0; q < n; ++q) {
+            SJob *j = sl.group[q];
+            img_ctx *c = j->ctx;
+            j->sigma.resize(c->hj.Q);
+            cudaMemcpyAsync(j->sigma.data(), c->hj.sigma, c->hj.Q * sizeof(double), cudaMemcpyDeviceToHost,
+                            sl.s);
+        }
+        cudaStreamSynchronize(sl.s);
+        const double t = now_ms();
+        for (int q = 0; q < n; ++q) {
+            SJob *j = sl.group[q];
+            fill_info(&j->info, sl.h_infos[q]);
+            j->st = (img_status)sl.h_infos[q].status;
+            j->t_done = t;
+            j->state = 2;
+            release(j->ctx);
+            j->ctx = nullptr;
+        }
+        inflight -= n;
+        sl.group.clear();
+        sl.busy = false;
+    }
+
+    void loop() {
+        cudaSetDevice(device);
+        std::unique_lock<std::mutex> lk(mu);
+        while (true) {
+            bool progressed = false;
+            for (auto &sl : slots) {
+                if (sl.busy && cudaEventQuery(sl.ev) == cudaSuccess) {
+                    finish(sl);
+                    progressed = true;
+                }
+            }
+            if (progressed) cv_done.notify_all();
+            // admission into free slots
+            for (auto &sl : slots) {
+                if (sl.busy || pending.empty()) continue;
+                std::vector<SJob *> group;
+                while (!pending.empty() && inflight + (int)group.size() < prm.max_inflight_jobs &&
+                       (int)group.size() < prm.max_batch) {
+                    SJob *j = pending.front();
+                    img_ctx *c = acquire(j);
+                    if (!c && inflight == 0 && group.empty()) {
+                        // nothing will free memory: drop pooled contexts of other shapes
+                        evict_free();
+                        c = acquire(j);
+                        if (!c) {                        // the job alone exceeds the budget
+                            pending.pop_front();
+                            j->st = IMG_ENOMEM;
+                            j->state = 2;
+                            j->t_done = now_ms();
+                            cv_done.notify_all();
+                            continue;
+                        }
+                    }
+                    if (!c) break;                       // wait for memory to free up
+                    j->ctx = c;
+                    pending.pop_front();
+                    group.push_back(j);
+                }
+                if (group.empty()) break;
+                img_status st = launch(sl, group);
+                if (st != IMG_OK) {
+                    fatal = st;
+                    for (SJob *j : group) {
+                        j->st = st;
+                        j->state = 2;
+                        j->t_done = now_ms();
+                        if (j->ctx) release(j->ctx);
+                        j->ctx = nullptr;
+                    }
+                    cv_done.notify_all();
+                }
+            }
+            const bool idle = inflight == 0 && pending.empty();
+            if (stop && idle) break;
+            if (idle) cv_work.wait(lk);
+            else cv_work.wait_for(lk, std::chrono::microseconds(100));
+        }
+    }
+};
+
+extern "C" {
+
+void img_server_params_default(img_server_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->hbm_budget_bytes = (size_t)8 << 30;
+    p->max_inflight_jobs = 0;
+    p->max_batch = 0;
+    p->n_streams = 4;
+}
+
+img_status img_server_create(const img_server_params *prm, img_server **out) {
+    if (!out || !prm) return IMG_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return IMG_ECUDA;
+    img_server *s = new (std::nothrow) img_server();
+    if (!s) return IMG_ENOMEM;
+    s->prm = *prm;
+    cudaGetDevice(&s->device);
+    int sms = 1;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+    if (s->prm.max_inflight_jobs <= 0) s->prm.max_inflight_jobs = 2 * sms;
+    if (s->prm.max_batch <= 0) s->prm.max_batch = s->prm.max_inflight_jobs;
+    if (s->prm.n_streams <= 0) s->prm.n_streams = 4;
+    s->slots.resize(s->prm.n_streams);
+    const int mb = s->prm.max_batch;
+    for (auto &sl : s->slots) {
+        if (cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMalloc(&sl.jobs, mb * sizeof(JobDev *)) != cudaSuccess ||
+            cudaMalloc(&sl.infos, mb * sizeof(DevInfo)) != cudaSuccess ||
+            cudaMallocHost(&sl.h_infos, mb * sizeof(DevInfo)) != cudaSuccess) {
+            img_server_destroy(s);
+            return IMG_ECUDA;
+        }
+    }
+    s->th = std::thread([s] { s->loop(); });
+    *out = s;
+    return IMG_OK;
+}
+
+img_status img_server_submit(img_server *s, const img_params *prm, const void *R, int dtype, long long N,
+                             long long *job_id) {
+    if (!s || !prm || !R || !job_id) return IMG_EINVAL;
+    if (dtype != IMG_C64 && dtype != IMG_C128) return IMG_EINVAL;
+    if (N <= prm->p) return IMG_EINVAL;
+    // validate by the same rules as img_create, without allocating
+    if (prm->p < 2 || prm->p > kMaxP || prm->n_l < 1 || prm->n_m < 1 || !prm->ant_xyz || !prm->l ||
+        !prm->m || !(prm->lambda > 0.0))
+        return IMG_EINVAL;
+    for (int k = 0; k < prm->p; ++k)
+        if (prm->ant_xyz[3 * k + 2] != 0.0) return IMG_EINVAL;
+    auto j = std::make_unique<SJob>();
+    j->prm = *prm;
+    j->ant.assign(prm->ant_xyz, prm->ant_xyz + 3 * prm->p);
+    j->l.assign(prm->l, prm->l + prm->n_l);
+    j->m.assign(prm->m, prm->m + prm->n_m);
+    const size_t pp = (size_t)prm->p * prm->p;
+    j->R.resize(2 * pp);
+    if (dtype == IMG_C128) std::memcpy(j->R.data(), R, 2 * pp * sizeof(double));
+    else
+        for (size_t e = 0; e < 2 * pp; ++e) j->R[e] = static_cast<const float *>(R)[e];
+    if (!finite_all(j->R.data(), j->R.size())) return IMG_EINVAL;
+    j->N = N;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->fatal != IMG_OK) return s->fatal;
+        j->id = s->next_id++;
+        j->t_submit = now_ms();
+        *job_id = j->id;
+        s->pending.push_back(j.get());
+        s->jobs.emplace(j->id, std::move(j));
+    }
+    s->cv_work.notify_all();
+    return IMG_OK;
+}
+
+img_status img_server_wait(img_server *s, long long job_id, double *sigma, img_solve_info *info,
+                           double timeout_ms, double *latency_ms) {
+    if (!s) return IMG_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->jobs.find(job_id);
+    if (it == s->jobs.end()) return IMG_EINVAL;
+    SJob *j = it->second.get();
+    const auto until = std::chrono::steady_clock::now() +
+                       std::chrono::microseconds((long long)(std::max(0.0, timeout_ms) * 1000.0));
+    while (j->state != 2) {
+        if (s->cv_done.wait_until(lk, until) == std::cv_status::timeout && j->state != 2) return IMG_ETIMEOUT;
+    }
+    if (sigma) std::memcpy(sigma, j->sigma.data(), j->sigma.size() * sizeof(double));
+    if (info) *info = j->info;
+    if (latency_ms) *latency_ms = j->t_done - j->t_submit;
+    const img_status st = j->st;
+    s->jobs.erase(it);
+    return st;
+}
+
+void img_server_destroy(img_server *s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->th.joinable()) s->th.join();
+    for (auto &sl : s->slots) {
+        if (sl.s) cudaStreamSynchronize(sl.s);
+        if (sl.jobs) cudaFree(sl.jobs);
+        if (sl.infos) cudaFree(sl.infos);
+        if (sl.h_infos) cudaFreeHost(sl.h_infos);
+        if (sl.ev) cudaEventDestroy(sl.ev);
+        if (sl.s) cudaStreamDestroy(sl.s);
+    }
+    for (img_ctx *c : s->all_ctx) img_destroy(c);
+    delete s;
+}
+
+}  // extern "C"
