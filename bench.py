@@ -25,6 +25,10 @@ import time
 
 import numpy as np
 
+# independent launch groups of the job server run on many streams; give them
+# as many hardware queues as CUDA allows (must precede CUDA initialisation)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -222,6 +226,57 @@ def run_ours(args, rank: int, world: int):
     return res
 
 
+# ---------------------------------------------------------------- serving
+def run_serve(args, rate: float = 200.0, seconds: float = 10.0, distinct: int = 48):
+    """Poisson arrivals of mixed jobs into the continuous-batching server;
+    latencies are the server's submit-to-done times."""
+    import synth
+    import paper_1505_01348_gb300 as G
+    prec = PRECISIONS[args.precision]
+    pool = [synth.serve_job_tc(j) for j in range(distinct)]
+    rng = np.random.default_rng(77)
+    n = int(rate * seconds)
+    gaps = rng.exponential(1.0 / rate, n)
+    srv = G.Server(hbm_budget_bytes=120 << 30)
+    shapes = {}
+    for j in pool:
+        shapes.setdefault((j.p, j.n_l, j.n_m), j)
+    for j in shapes.values():                            # pool contexts before the clock starts
+        srv.reserve(j, 2 * sm_count(), precision=prec)
+    ids = []
+    t0 = time.perf_counter()
+    t_next = t0
+    for k in range(n):
+        t_next += gaps[k]
+        dt = t_next - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        ids.append(srv.submit_job(pool[k % distinct], precision=prec))
+    lat = []
+    for jid in ids:
+        _, info, ms = srv.wait(jid)
+        lat.append(ms)
+    t_end = time.perf_counter()
+    srv.close()
+    lat = np.array(lat)
+    # the plain per-job FP32 path: one job at a time through img_solve
+    sample = pool[:6]
+    t1 = time.perf_counter()
+    for job in sample:
+        im = G.Imager.from_job(job, precision=0)
+        im.solve()
+        im.close()
+    per_job = len(sample) / (time.perf_counter() - t1)
+    return {"rate_jobs_s": rate, "jobs": n, "offered_s": seconds,
+            "images_s": n / (t_end - t0), "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()),
+            "mix": f"{distinct} distinct seeded jobs cycled: p in {{32,64}}, 64^2 or 128^2 grid, "
+                   "5-50 sources, N=1e4; arrivals Poisson",
+            "precision": args.precision,
+            "per_job_fp32_images_s": per_job,
+            "per_job_fp32_sample": f"{len(sample)} jobs of the mix, one img_solve at a time"}
+
+
 # ---------------------------------------------------------------- oracle timing
 def oracle_sample(budget_passes: int = 40, seed: int = 2000):
     """Time the FP64 oracle on one image of the same workload: full setup
@@ -304,6 +359,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -362,6 +418,8 @@ def main():
             "clocks": r["clocks"],
             "e2e": r["e2e"],
         }
+        if not args.no_serve and world == 1:
+            line["serve"] = run_serve(args)
         if not args.no_cpu and world == 1:
             line["cpu_baseline"] = cpu_baseline_line(oracle_passes_per_image())
         print(json.dumps(line), flush=True)

@@ -132,6 +132,8 @@ typedef struct {
     double cyc_lsqr;     /* ... of which in LSQR subproblems                 */
     double cyc_lsqr_fwd; /* ... of which in LSQR's forward products M v      */
     double cyc_lsqr_adj; /* ... of which in LSQR's adjoint products M^H u    */
+    double t_begin_ns;   /* device global timer when the job's CTA started   */
+    double t_end_ns;     /* ... and when it finished                         */
 } img_solve_info;
 
 /* Fill *prm with defaults: PWLS, MVDR bound, C = 1, no inflation, kappa 6,
@@ -245,15 +247,29 @@ typedef struct img_server img_server;
 typedef struct {
     size_t hbm_budget_bytes;    /* device memory for pooled job contexts        */
     int max_inflight_jobs;      /* jobs on the GPU at once (0: 2 x SM count)     */
-    int max_batch;              /* jobs per launch group (0: max_inflight_jobs)  */
-    int n_streams;              /* launch streams (0: 4)                         */
+    int max_batch;              /* most jobs per launch group (0: 2); a free
+                                   stream takes ceil(pending / free streams)    */
+    int n_streams;              /* launch streams (0: 128, the number of kernels
+                                   a GB300 runs at once)                        */
+    int max_pixels;             /* largest Q accepted (0: 65536); sizes the
+                                   pinned result buffers made at creation       */
 } img_server_params;
 
-/* Defaults: 8 GiB budget, 0, 0, 4 streams. */
+/* Defaults: 8 GiB budget, 2 x SMs in flight, groups of up to 2, 128 streams,
+ * 65536 pixels.  Nothing is allocated while jobs run except job contexts of a
+ * shape the pool lacks (img_server_reserve avoids even that).
+ * Independent streams only overlap when CUDA_DEVICE_MAX_CONNECTIONS (set
+ * before CUDA initialises) gives them separate hardware queues; 32 is the
+ * most CUDA allows. */
 void img_server_params_default(img_server_params *p);
 img_status img_server_create(const img_server_params *prm, img_server **out);
+/* Pre-create `count` pooled contexts for jobs shaped like *prm (p, n_l, n_m
+ * and support cap), so that admission later allocates nothing.  IMG_ENOMEM
+ * when the budget holds fewer (those that fit are kept). */
+img_status img_server_reserve(img_server *s, const img_params *prm, int count);
 /* Queue one job: *prm describes it as for img_create (arrays copied), R and N
- * as for img_set_covariance (host memory, copied).  *job_id identifies it. */
+ * as for img_set_covariance (host memory, copied).  *job_id identifies it.
+ * IMG_EINVAL for jobs with more than max_pixels pixels. */
 img_status img_server_submit(img_server *s, const img_params *prm, const void *R, int dtype,
                              long long N, long long *job_id);
 /* Wait up to timeout_ms for job_id; on completion copy its image (Q doubles,

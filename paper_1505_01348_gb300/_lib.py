@@ -25,7 +25,7 @@ EXPORTS = ("img_params_default", "img_create", "img_set_covariance", "img_dirty"
            "img_mvdr_bound", "img_solve", "img_get_sets", "img_get_gradient", "img_get_events",
            "img_psi",
            "img_psi_adj", "img_prepare_batch", "img_solve_batch", "img_psi_noalloc",
-           "img_server_params_default", "img_server_create", "img_server_submit",
+           "img_server_params_default", "img_server_create", "img_server_reserve", "img_server_submit",
            "img_server_wait", "img_server_destroy", "img_destroy", "img_status_str")
 
 
@@ -46,7 +46,7 @@ class SolveInfo(C.Structure):
                 ("lambda_min", C.c_double), ("op_flops", C.c_double),
                 ("cyc_total", C.c_double), ("cyc_gradient", C.c_double),
                 ("cyc_lsqr", C.c_double), ("cyc_lsqr_fwd", C.c_double),
-                ("cyc_lsqr_adj", C.c_double)]
+                ("cyc_lsqr_adj", C.c_double), ("t_begin_ns", C.c_double), ("t_end_ns", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -54,7 +54,7 @@ class SolveInfo(C.Structure):
 
 class ServerParams(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_inflight_jobs", C.c_int),
-                ("max_batch", C.c_int), ("n_streams", C.c_int)]
+                ("max_batch", C.c_int), ("n_streams", C.c_int), ("max_pixels", C.c_int)]
 
 
 class ImgError(RuntimeError):
@@ -113,6 +113,8 @@ def load(build_if_missing: bool = False) -> C.CDLL:
     lib.img_server_params_default.restype = None
     lib.img_server_create.argtypes = [C.POINTER(ServerParams), C.POINTER(vp)]
     lib.img_server_create.restype = i
+    lib.img_server_reserve.argtypes = [vp, C.POINTER(ImgParams), i]
+    lib.img_server_reserve.restype = i
     lib.img_server_submit.argtypes = [vp, C.POINTER(ImgParams), dp, i, ll, C.POINTER(ll)]
     lib.img_server_submit.restype = i
     lib.img_server_wait.argtypes = [vp, ll, dp, C.POINTER(SolveInfo), C.c_double, C.POINTER(C.c_double)]
@@ -306,7 +308,8 @@ def solve_batch(imagers, outs=None, allow=(IMG_ENOTCONV,)):
 class Server:
     """Continuous-batching job server (wraps img_server)."""
 
-    def __init__(self, hbm_budget_bytes=None, max_inflight_jobs=0, max_batch=0, n_streams=0):
+    def __init__(self, hbm_budget_bytes=None, max_inflight_jobs=0, max_batch=0, n_streams=0,
+                 max_pixels=0):
         self._lib = load()
         sp = ServerParams()
         self._lib.img_server_params_default(C.byref(sp))
@@ -316,10 +319,27 @@ class Server:
         sp.max_batch = int(max_batch)
         if n_streams:
             sp.n_streams = int(n_streams)
+        if max_pixels:
+            sp.max_pixels = int(max_pixels)
         h = C.c_void_p()
         _check(self._lib.img_server_create(C.byref(sp), C.byref(h)), "img_server_create")
         self.h = h
         self._Q = {}
+
+    def reserve(self, job, count: int, **kw):
+        """Pre-create `count` pooled contexts shaped like `job`."""
+        ant = np.ascontiguousarray(job.ant_xyz, dtype=np.float64)
+        l = np.ascontiguousarray(job.l, dtype=np.float64)
+        m = np.ascontiguousarray(job.m, dtype=np.float64)
+        prm = default_params()
+        prm.p, prm.n_l, prm.n_m = ant.shape[0], l.shape[0], m.shape[0]
+        prm.ant_xyz = ant.ctypes.data_as(C.POINTER(C.c_double))
+        prm.l = l.ctypes.data_as(C.POINTER(C.c_double))
+        prm.m = m.ctypes.data_as(C.POINTER(C.c_double))
+        prm.lambda_ = float(job.lam)
+        for k, v in kw.items():
+            setattr(prm, k, v)
+        _check(self._lib.img_server_reserve(self.h, C.byref(prm), int(count)), "img_server_reserve")
 
     def submit(self, ant_xyz, l, m, lam, R, N, **kw) -> int:
         ant = np.ascontiguousarray(ant_xyz, dtype=np.float64)

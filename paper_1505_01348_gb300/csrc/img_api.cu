@@ -210,6 +210,8 @@ void fill_info(img_solve_info *o, const DevInfo &d) {
     o->cyc_lsqr = d.cyc_lsqr;
     o->cyc_lsqr_fwd = d.cyc_lsqr_fwd;
     o->cyc_lsqr_adj = d.cyc_lsqr_adj;
+    o->t_begin_ns = (double)d.t_begin_ns;
+    o->t_end_ns = (double)d.t_end_ns;
 }
 
 }  // namespace
@@ -675,8 +677,23 @@ struct SSlot {                           // one launch stream and its workspace
     DevInfo *infos = nullptr;
     int *status = nullptr;
     DevInfo *h_infos = nullptr;          // pinned
+    char *h_stage = nullptr;             // pinned staging of the group's inputs
+    size_t stage_cap = 0, stage_off = 0;
+    double *h_sigma = nullptr;           // pinned images of the group (grown on demand)
+    size_t sigma_cap = 0;
+    std::vector<size_t> sigma_off;
     std::vector<SJob *> group;
     bool busy = false;
+
+    // Pinned copy of `bytes` from src; falls back to the (pageable) source
+    // when the arena is full.
+    const void *stage(const void *src, size_t bytes) {
+        const size_t off = (stage_off + 255) & ~size_t(255);
+        if (!h_stage || off + bytes > stage_cap) return src;
+        std::memcpy(h_stage + off, src, bytes);
+        stage_off = off + bytes;
+        return h_stage + off;
+    }
 };
 
 using ShapeKey = std::tuple<int, int, int, int>;   // p, n_l, n_m, support cap
@@ -688,8 +705,10 @@ ShapeKey key_of(const img_params &p) {
 }
 
 // Load a job's parameters, geometry and covariance into a pooled context of
-// the same shape (asynchronous on stream s).
-img_status reconfigure(img_ctx *c, SJob *j, cudaStream_t s) {
+// the same shape (asynchronous on the slot's stream, inputs staged in the
+// slot's pinned arena).
+img_status reconfigure(img_ctx *c, SJob *j, SSlot &sl) {
+    cudaStream_t s = sl.s;
     JobDev &J = c->hj;
     const img_params &P = j->prm;
     c->prm = P;
@@ -716,14 +735,17 @@ img_status reconfigure(img_ctx *c, SJob *j, cudaStream_t s) {
     J.feas_tol = P.feas_tol;
     J.N = j->N;
     const int p = P.p;
-    CK(cudaMemcpyAsync((void *)J.ant, c->ant.data(), 3 * p * sizeof(double), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync((void *)J.lg, c->l.data(), P.n_l * sizeof(double), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync((void *)J.mg, c->m.data(), P.n_m * sizeof(double), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(J.R64, j->R.data(), (size_t)p * p * sizeof(double2), cudaMemcpyHostToDevice, s));
+    auto h2d = [&](void *dst, const void *src, size_t bytes) {
+        return cudaMemcpyAsync(dst, sl.stage(src, bytes), bytes, cudaMemcpyHostToDevice, s);
+    };
+    CK(h2d((void *)J.ant, c->ant.data(), 3 * p * sizeof(double)));
+    CK(h2d((void *)J.lg, c->l.data(), P.n_l * sizeof(double)));
+    CK(h2d((void *)J.mg, c->m.data(), P.n_m * sizeof(double)));
+    CK(h2d(J.R64, j->R.data(), (size_t)p * p * sizeof(double2)));
     CK(cudaMemsetAsync(J.flags, 0xff, sizeof(int), s));
     CK(cudaMemsetAsync(J.flags + 1, 0, sizeof(int), s));
-    CK(cudaMemcpyAsync(c->dj, &J, sizeof(JobDev), cudaMemcpyHostToDevice, s));
-    CK(img::launch_tables(c->djp, 1, s));
+    CK(h2d(c->dj, &J, sizeof(JobDev)));
+    // the steering tables are recomputed inside the job's kernel
     c->has_cov = true;
     c->prepared = false;
     c->solved = false;
@@ -799,49 +821,55 @@ struct img_server {
     img_status launch(SSlot &sl, std::vector<SJob *> &group) {
         const int n = (int)group.size();
         std::vector<img_ctx *> ctxs(n);
+        sl.stage_off = 0;
         for (int q = 0; q < n; ++q) {
             ctxs[q] = group[q]->ctx;
-            img_status st = reconfigure(ctxs[q], group[q], sl.s);
+            img_status st = reconfigure(ctxs[q], group[q], sl);
             if (st != IMG_OK) return st;
-            group[q]->t_start = now_ms();
-            group[q]->state = 1;
         }
         const Groups g = group_by_mode(ctxs.data(), n);
         std::vector<JobDev *> ptrs(n);
         for (int q = 0; q < n; ++q) ptrs[q] = ctxs[g.order[q]]->dj;
-        CK(cudaMemcpyAsync(sl.jobs, ptrs.data(), n * sizeof(JobDev *), cudaMemcpyHostToDevice, sl.s));
+        CK(cudaMemcpyAsync(sl.jobs, sl.stage(ptrs.data(), n * sizeof(JobDev *)), n * sizeof(JobDev *),
+                           cudaMemcpyHostToDevice, sl.s));
         for (int md = 0; md < 3; ++md) {
             const int nb = g.end[md] - g.begin[md];
             if (!nb) continue;
             JobDev *const *jp = sl.jobs + g.begin[md];
-            CK(img::launch_factor(jp, nb, sl.s));
-            CK(img::launch_bounds(jp, nb, g.max_tiles[md], g.max_p[md], md, sl.s));
-            CK(img::launch_finalize(jp, nb, sl.s, nullptr));
-            CK(img::launch_solve(jp, nb, g.max_p[md], md, sl.infos + g.begin[md], nullptr, sl.s));
+            CK(img::launch_job(jp, nb, g.max_p[md], md, sl.infos + g.begin[md], nullptr, sl.s));
         }
         CK(cudaMemcpyAsync(sl.h_infos, sl.infos, n * sizeof(DevInfo), cudaMemcpyDeviceToHost, sl.s));
-        CK(cudaEventRecord(sl.ev, sl.s));
-        // results in job order: remember the permutation through group order
+        // results in group order: remember the permutation
         sl.group.assign(n, nullptr);
         for (int q = 0; q < n; ++q) sl.group[q] = group[g.order[q]];
+        // pinned result space was sized at creation (max_batch x max_pixels);
+        // allocating pinned memory here would synchronise with running jobs
+        size_t need = 0;
+        sl.sigma_off.assign(n, 0);
+        for (int q = 0; q < n; ++q) {
+            sl.sigma_off[q] = need;
+            need += sl.group[q]->ctx->hj.Q;
+        }
+        if (need > sl.sigma_cap) return IMG_ENOMEM;
+        for (int q = 0; q < n; ++q) {
+            img_ctx *c = sl.group[q]->ctx;
+            CK(cudaMemcpyAsync(sl.h_sigma + sl.sigma_off[q], c->hj.sigma, c->hj.Q * sizeof(double),
+                               cudaMemcpyDeviceToHost, sl.s));
+        }
+        CK(cudaEventRecord(sl.ev, sl.s));
         sl.busy = true;
-        inflight += n;
         return IMG_OK;
     }
 
+    // Publish a completed group (results already in the slot's pinned
+    // buffers).  Called with the lock held; makes no CUDA calls.
     void finish(SSlot &sl) {
         const int n = (int)sl.group.size();
-        for (int q = 0; q < n; ++q) {
-            SJob *j = sl.group[q];
-            img_ctx *c = j->ctx;
-            j->sigma.resize(c->hj.Q);
-            cudaMemcpyAsync(j->sigma.data(), c->hj.sigma, c->hj.Q * sizeof(double), cudaMemcpyDeviceToHost,
-                            sl.s);
-        }
-        cudaStreamSynchronize(sl.s);
         const double t = now_ms();
         for (int q = 0; q < n; ++q) {
             SJob *j = sl.group[q];
+            const int Q = j->ctx->hj.Q;
+            j->sigma.assign(sl.h_sigma + sl.sigma_off[q], sl.h_sigma + sl.sigma_off[q] + Q);
             fill_info(&j->info, sl.h_infos[q]);
             j->st = (img_status)sl.h_infos[q].status;
             j->t_done = t;
@@ -854,62 +882,91 @@ struct img_server {
         sl.busy = false;
     }
 
+    // Scheduler: poll completions and launch admitted groups outside the
+    // lock; hold it only to move jobs between the queue, the slots and done.
     void loop() {
         cudaSetDevice(device);
-        std::unique_lock<std::mutex> lk(mu);
+        std::vector<SSlot *> done, idle;
+        std::vector<std::pair<SSlot *, std::vector<SJob *>>> plan;
         while (true) {
-            bool progressed = false;
-            for (auto &sl : slots) {
-                if (sl.busy && cudaEventQuery(sl.ev) == cudaSuccess) {
-                    finish(sl);
-                    progressed = true;
+            done.clear();
+            for (auto &sl : slots)
+                if (sl.busy && cudaEventQuery(sl.ev) == cudaSuccess) done.push_back(&sl);
+            plan.clear();
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                for (SSlot *sl : done) finish(*sl);
+                if (!done.empty()) cv_done.notify_all();
+                // admission: each free slot takes its share of the pending jobs
+                // (one job per launch at low load, up to max_batch when jobs
+                // outnumber free slots)
+                idle.clear();
+                for (auto &sl : slots)
+                    if (!sl.busy) idle.push_back(&sl);
+                int free_slots = (int)idle.size();
+                for (SSlot *sl : idle) {
+                    if (pending.empty()) break;
+                    const int share = std::max(1, std::min(prm.max_batch,
+                                                           ((int)pending.size() + free_slots - 1) / free_slots));
+                    --free_slots;
+                    std::vector<SJob *> group;
+                    while (!pending.empty() && inflight < prm.max_inflight_jobs && (int)group.size() < share) {
+                        SJob *j = pending.front();
+                        img_ctx *c = acquire(j);
+                        if (!c && inflight == 0 && plan.empty() && group.empty()) {
+                            // nothing will free memory: drop pooled contexts of other shapes
+                            evict_free();
+                            c = acquire(j);
+                            if (!c) {                    // the job alone exceeds the budget
+                                pending.pop_front();
+                                j->st = IMG_ENOMEM;
+                                j->state = 2;
+                                j->t_done = now_ms();
+                                cv_done.notify_all();
+                                continue;
+                            }
+                        }
+                        if (!c) break;                   // wait for memory to free up
+                        j->ctx = c;
+                        j->state = 1;
+                        j->t_start = now_ms();
+                        pending.pop_front();
+                        group.push_back(j);
+                        ++inflight;
+                    }
+                    if (group.empty()) break;
+                    sl->busy = true;                     // reserved for this plan
+                    plan.emplace_back(sl, std::move(group));
+                }
+                const bool quiet = inflight == 0 && pending.empty() && plan.empty();
+                if (stop && quiet) break;
+                if (quiet) {
+                    cv_work.wait(lk);
+                    continue;
                 }
             }
-            if (progressed) cv_done.notify_all();
-            // admission into free slots
-            for (auto &sl : slots) {
-                if (sl.busy || pending.empty()) continue;
-                std::vector<SJob *> group;
-                while (!pending.empty() && inflight + (int)group.size() < prm.max_inflight_jobs &&
-                       (int)group.size() < prm.max_batch) {
-                    SJob *j = pending.front();
-                    img_ctx *c = acquire(j);
-                    if (!c && inflight == 0 && group.empty()) {
-                        // nothing will free memory: drop pooled contexts of other shapes
-                        evict_free();
-                        c = acquire(j);
-                        if (!c) {                        // the job alone exceeds the budget
-                            pending.pop_front();
-                            j->st = IMG_ENOMEM;
-                            j->state = 2;
-                            j->t_done = now_ms();
-                            cv_done.notify_all();
-                            continue;
-                        }
-                    }
-                    if (!c) break;                       // wait for memory to free up
-                    j->ctx = c;
-                    pending.pop_front();
-                    group.push_back(j);
-                }
-                if (group.empty()) break;
-                img_status st = launch(sl, group);
+            for (auto &pg : plan) {
+                img_status st = launch(*pg.first, pg.second);
                 if (st != IMG_OK) {
+                    std::lock_guard<std::mutex> lk(mu);
                     fatal = st;
-                    for (SJob *j : group) {
+                    for (SJob *j : pg.second) {
                         j->st = st;
                         j->state = 2;
                         j->t_done = now_ms();
                         if (j->ctx) release(j->ctx);
                         j->ctx = nullptr;
+                        --inflight;
                     }
+                    pg.first->busy = false;
+                    pg.first->group.clear();
                     cv_done.notify_all();
                 }
             }
-            const bool idle = inflight == 0 && pending.empty();
-            if (stop && idle) break;
-            if (idle) cv_work.wait(lk);
-            else cv_work.wait_for(lk, std::chrono::microseconds(100));
+            if (plan.empty() && done.empty()) {
+                std::unique_lock<std::mutex> lk(mu);
+                cv_work.wait_for(lk, std::chrono::microseconds(200));
+            }
         }
     }
 };
@@ -921,8 +978,9 @@ void img_server_params_default(img_server_params *p) {
     std::memset(p, 0, sizeof(*p));
     p->hbm_budget_bytes = (size_t)8 << 30;
     p->max_inflight_jobs = 0;
-    p->max_batch = 0;
-    p->n_streams = 4;
+    p->max_batch = 2;
+    p->n_streams = 128;
+    p->max_pixels = 65536;
 }
 
 img_status img_server_create(const img_server_params *prm, img_server **out) {
@@ -937,8 +995,9 @@ img_status img_server_create(const img_server_params *prm, img_server **out) {
     int sms = 1;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
     if (s->prm.max_inflight_jobs <= 0) s->prm.max_inflight_jobs = 2 * sms;
-    if (s->prm.max_batch <= 0) s->prm.max_batch = s->prm.max_inflight_jobs;
-    if (s->prm.n_streams <= 0) s->prm.n_streams = 4;
+    if (s->prm.max_batch <= 0) s->prm.max_batch = 2;
+    if (s->prm.n_streams <= 0) s->prm.n_streams = 128;
+    if (s->prm.max_pixels <= 0) s->prm.max_pixels = 65536;
     s->slots.resize(s->prm.n_streams);
     const int mb = s->prm.max_batch;
     for (auto &sl : s->slots) {
@@ -946,7 +1005,10 @@ img_status img_server_create(const img_server_params *prm, img_server **out) {
             cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess ||
             cudaMalloc(&sl.jobs, mb * sizeof(JobDev *)) != cudaSuccess ||
             cudaMalloc(&sl.infos, mb * sizeof(DevInfo)) != cudaSuccess ||
-            cudaMallocHost(&sl.h_infos, mb * sizeof(DevInfo)) != cudaSuccess) {
+            cudaMallocHost(&sl.h_infos, mb * sizeof(DevInfo)) != cudaSuccess ||
+            cudaMallocHost(&sl.h_stage, sl.stage_cap = (size_t)mb * (64 << 10) + (4 << 20)) != cudaSuccess ||
+            cudaMallocHost(&sl.h_sigma, (sl.sigma_cap = (size_t)mb * s->prm.max_pixels) * sizeof(double)) !=
+                cudaSuccess) {
             img_server_destroy(s);
             return IMG_ECUDA;
         }
@@ -956,11 +1018,30 @@ img_status img_server_create(const img_server_params *prm, img_server **out) {
     return IMG_OK;
 }
 
+img_status img_server_reserve(img_server *s, const img_params *prm, int count) {
+    if (!s || !prm || count < 0) return IMG_EINVAL;
+    SJob probe;
+    probe.prm = *prm;
+    probe.ant.assign(prm->ant_xyz, prm->ant_xyz + 3 * prm->p);
+    probe.l.assign(prm->l, prm->l + prm->n_l);
+    probe.m.assign(prm->m, prm->m + prm->n_m);
+    std::lock_guard<std::mutex> lk(s->mu);
+    std::vector<img_ctx *> got;
+    for (int k = 0; k < count; ++k) {
+        img_ctx *c = s->acquire(&probe);
+        if (!c) break;
+        got.push_back(c);
+    }
+    for (img_ctx *c : got) s->release(c);
+    return (int)got.size() == count ? IMG_OK : IMG_ENOMEM;
+}
+
 img_status img_server_submit(img_server *s, const img_params *prm, const void *R, int dtype, long long N,
                              long long *job_id) {
     if (!s || !prm || !R || !job_id) return IMG_EINVAL;
     if (dtype != IMG_C64 && dtype != IMG_C128) return IMG_EINVAL;
     if (N <= prm->p) return IMG_EINVAL;
+    if ((long long)prm->n_l * prm->n_m > s->prm.max_pixels) return IMG_EINVAL;
     // validate by the same rules as img_create, without allocating
     if (prm->p < 2 || prm->p > kMaxP || prm->n_l < 1 || prm->n_m < 1 || !prm->ant_xyz || !prm->l ||
         !prm->m || !(prm->lambda > 0.0))
@@ -1025,6 +1106,8 @@ void img_server_destroy(img_server *s) {
         if (sl.jobs) cudaFree(sl.jobs);
         if (sl.infos) cudaFree(sl.infos);
         if (sl.h_infos) cudaFreeHost(sl.h_infos);
+        if (sl.h_stage) cudaFreeHost(sl.h_stage);
+        if (sl.h_sigma) cudaFreeHost(sl.h_sigma);
         if (sl.ev) cudaEventDestroy(sl.ev);
         if (sl.s) cudaStreamDestroy(sl.s);
     }

@@ -23,6 +23,8 @@ struct DevInfo {
     double cyc_lsqr;
     double cyc_lsqr_fwd;
     double cyc_lsqr_adj;
+    unsigned long long t_begin_ns;   // device global timer at the job's start and end
+    unsigned long long t_end_ns;
 };
 
 // Everything one imaging job keeps on the device.  All pointers are device
@@ -89,6 +91,9 @@ cudaError_t launch_finalize(JobDev *const *jobs, int n, cudaStream_t st, int *ba
 // mode: 0 CUDA-core FP32 operators, 1 tensor cores FP16x3, 2 tensor cores BF16x3
 cudaError_t launch_solve(JobDev *const *jobs, int n, int max_p, int mode, DevInfo *batch_info,
                          double *const *sigma_out, cudaStream_t st);
+// Factor, bounds and solve of each job inside its own CTA (one launch).
+cudaError_t launch_job(JobDev *const *jobs, int n, int max_p, int mode, DevInfo *batch_info,
+                       double *const *sigma_out, cudaStream_t st);
 cudaError_t launch_psi(const JobDev *job_dev, const float *wx, float2 *part, int nparts, int Q,
                        int p, int mode, double2 *Kout, cudaStream_t st);
 cudaError_t launch_psi_adj(const JobDev *job_dev, const float2 *U, double *out, int Q, int p,

@@ -9,6 +9,9 @@
 //               (Table I, Sec. V-A, Sec. V-B)
 #include "cta_ops.cuh"
 #include "tc_ops.cuh"
+
+#include <mutex>
+#include <unordered_map>
 #include "../../include/img.h"
 
 namespace img {
@@ -17,12 +20,12 @@ namespace img {
 // El[il*p+k] = p^{-1/2} exp(-j 2 pi x_k l_il / lam), Em[im*p+k] = exp(-j 2 pi y_k m_im / lam).
 // The phase argument t is reduced to r = t - rint(t) in FP64 before sincospi,
 // so phases of hundreds of turns keep full accuracy.
-__global__ void k_tables(JobDev *const *jobs) {
-    const JobDev &J = *jobs[blockIdx.y];
+// Tables of one job by the threads [t0, t0 + nt) of the grid dimension used.
+__device__ void tables_job(const JobDev &J, int t0, int nt) {
     const int p = J.p;
     const int total = p * (J.n_l + J.n_m);
     const double sc = rsqrt((double)p);
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    for (int e = t0; e < total; e += nt) {
         const bool isl = e < p * J.n_l;
         const int e2 = isl ? e : e - p * J.n_l;
         const int g = e2 / p, k = e2 - g * p;
@@ -37,11 +40,14 @@ __global__ void k_tables(JobDev *const *jobs) {
     }
 }
 
+__global__ void k_tables(JobDev *const *jobs) {
+    tables_job(*jobs[blockIdx.y], blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
 // ---------------------------------------------------------------- factor
 // Right-looking Cholesky in FP64, then L^-1 by forward substitution (one
 // column per thread) and R^-1 = L^-H L^-1.  Status 0 ok, IMG_ENOTPD else.
-__global__ void k_factor(JobDev *const *jobs) {
-    const JobDev &J = *jobs[blockIdx.x];
+__device__ void factor_job(const JobDev &J) {
     const int p = J.p;
     double2 *L = J.L64;
     __shared__ int bad;
@@ -118,6 +124,8 @@ __global__ void k_factor(JobDev *const *jobs) {
     }
     if (threadIdx.x == 0) J.flags[0] = 0;
 }
+
+__global__ void k_factor(JobDev *const *jobs) { factor_job(*jobs[blockIdx.x]); }
 
 // ---------------------------------------------------------------- bounds
 // dirty_i = Re(a_i^H R a_i) and h_i = Re(a_i^H R^-1 a_i) for all pixels
@@ -224,10 +232,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_psi_adj_tc(const JobDev *Jp, co
 //   C = N/(N-p) or 1; mvdr = C/h; D = h^2/C; std_MF = dirty/sqrt(N);
 //   std_MVDR = mvdr/sqrt(N-p-1); gamma = chosen image, optionally inflated;
 //   PWLS: x = D sigma (scale 1/D, upper D gamma); eps = kappa std with a floor.
-__global__ void k_finalize(JobDev *const *jobs, int *batch_status) {
-    const JobDev &J = *jobs[blockIdx.x];
-    if (batch_status && threadIdx.x == 0) batch_status[blockIdx.x] = J.flags[0];
-    if (J.flags[0] != 0) return;
+__device__ void finalize_job(const JobDev &J) {
     __shared__ double sbuf[kThreads / 32];
     const double C = J.bias_c ? (double)J.N / (double)(J.N - J.p) : 1.0;
     const double sqN = sqrt((double)J.N);
@@ -264,6 +269,14 @@ __global__ void k_finalize(JobDev *const *jobs, int *batch_status) {
     const float fl = (float)(J.eps_floor * mx);
     for (int i = threadIdx.x; i < J.Q; i += blockDim.x) J.eps[i] = fmaxf(J.eps[i], fl);
     if (threadIdx.x == 0) J.flags[1] = 1;
+    __syncthreads();
+}
+
+__global__ void k_finalize(JobDev *const *jobs, int *batch_status) {
+    const JobDev &J = *jobs[blockIdx.x];
+    if (batch_status && threadIdx.x == 0) batch_status[blockIdx.x] = J.flags[0];
+    if (J.flags[0] != 0) return;
+    finalize_job(J);
 }
 
 // ---------------------------------------------------------------- solver
@@ -574,7 +587,7 @@ __device__ void supp_remove(const JobDev &J, int i, int &ns) {
 
 // Persistent active-set driver (Table I), one CTA per job.  MODE selects the
 // adjoint's arithmetic (0 CUDA cores FP32, 1 tensor cores FP16x3, 2 BF16x3).
-template <int MODE>
+template <int MODE, bool PREP>
 __global__ void __launch_bounds__(kThreads, 1)
 k_solve(JobDev *const *jobs, DevInfo *batch_info, double *const *sigma_out) {
     const JobDev &J = *jobs[blockIdx.x];
@@ -588,20 +601,37 @@ k_solve(JobDev *const *jobs, DevInfo *batch_info, double *const *sigma_out) {
     __shared__ uint32_t tc_slot;
     DevInfo info{};
     info.status = IMG_OK;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(info.t_begin_ns));
+    const int p = J.p, Q = J.Q;
+    const bool pwls = J.cost == IMG_COST_PWLS;
+    // tensor memory is allocated once per CTA (the permit is relinquished)
+    TcWork T{};
+    if constexpr (MODE != 0) {
+        tc_carve(T, dyn, p);
+        tc_setup(T, tc_bar, &tc_slot, p);
+    }
+    if constexpr (PREP) {
+        // the whole job in this CTA: steering tables, factor, dirty image and
+        // MVDR denominators (the adjoint of k_bounds), bounds and thresholds
+        tables_job(J, threadIdx.x, blockDim.x);
+        __syncthreads();
+        factor_job(J);
+        __syncthreads();
+        if (J.flags[0] == 0) {
+            adjoint_full<MODE>(J, J.R32, A, T, S.red, S.dbuf, [&](int i, float v) { J.dirty[i] = v; });
+            adjoint_full<MODE>(J, J.Ri32, A, T, S.red, S.dbuf, [&](int i, float v) { J.h[i] = v; });
+            finalize_job(J);
+        }
+        __syncthreads();
+    }
     if (J.flags[0] != 0 || J.flags[1] != 1) {
         info.status = J.flags[0] != 0 ? J.flags[0] : IMG_EINVAL;
         if (threadIdx.x == 0) {
             *J.info = info;
             if (batch_info) batch_info[blockIdx.x] = info;
         }
+        if constexpr (MODE != 0) tc_teardown(T, p);
         return;
-    }
-    const int p = J.p, Q = J.Q;
-    const bool pwls = J.cost == IMG_COST_PWLS;
-    TcWork T{};
-    if constexpr (MODE != 0) {
-        tc_carve(T, dyn, p);
-        tc_setup(T, tc_bar, &tc_slot, p);
     }
     for (int i = threadIdx.x; i < Q; i += blockDim.x) {
         J.x[i] = 0.0;
@@ -786,6 +816,7 @@ k_solve(JobDev *const *jobs, DevInfo *batch_info, double *const *sigma_out) {
         info.converged = converged ? 1 : 0;
         info.lambda_min = lam_min;
         info.cyc_total = (double)(clock64() - t_start);
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(info.t_end_ns));
         *J.ev_count = nev;
         *J.info = info;
         if (batch_info) batch_info[blockIdx.x] = info;
@@ -944,6 +975,26 @@ size_t bounds_smem_bytes(int p) {
     return (size_t)p * kTile * sizeof(float2) + (kTile + 16 * kTile) * sizeof(float);
 }
 
+// Raise a kernel's dynamic shared-memory limit (and prefer the maximum
+// shared-memory carve-out) only when a launch needs more than any before:
+// changing a function's attributes while instances of it run can hold the
+// launch back, which serialised independent launches on separate streams.
+static std::mutex g_attr_mu;
+static std::unordered_map<const void *, size_t> g_attr;
+
+static cudaError_t ensure_smem(const void *func, size_t bytes) {
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+    auto it = g_attr.find(func);
+    if (it != g_attr.end() && it->second >= bytes) return cudaSuccess;
+    const size_t want = bytes < 48 * 1024 ? 48 * 1024 : bytes;
+    cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    g_attr[func] = want;
+    return cudaSuccess;
+}
+
 static int g_num_sms = 0;
 static int num_sms() {
     if (!g_num_sms) {
@@ -968,7 +1019,7 @@ cudaError_t launch_factor(JobDev *const *jobs, int n, cudaStream_t st) {
 template <int MODE>
 static cudaError_t launch_bounds_tc_t(JobDev *const *jobs, int n, int max_tiles, int max_p, cudaStream_t st) {
     const size_t sm = tc_smem_bytes(max_p) + 1024;
-    cudaError_t e = cudaFuncSetAttribute(k_bounds_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = ensure_smem((const void *)k_bounds_tc<MODE>, sm);
     if (e != cudaSuccess) return e;
     int per_job = (num_sms() + n - 1) / n;
     per_job = max(1, min(per_job, max_tiles));
@@ -980,7 +1031,7 @@ cudaError_t launch_bounds(JobDev *const *jobs, int n, int max_tiles, int max_p, 
     if (mode == 1) return launch_bounds_tc_t<1>(jobs, n, (max_tiles + 1) / 2, max_p, st);
     if (mode == 2) return launch_bounds_tc_t<2>(jobs, n, (max_tiles + 1) / 2, max_p, st);
     const size_t sm = bounds_smem_bytes(max_p);
-    cudaError_t e = cudaFuncSetAttribute(k_bounds, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = ensure_smem((const void *)k_bounds, sm);
     if (e != cudaSuccess) return e;
     int per_job = (2 * num_sms() + n - 1) / n;
     per_job = max(1, min(per_job, max_tiles));
@@ -993,21 +1044,33 @@ cudaError_t launch_finalize(JobDev *const *jobs, int n, cudaStream_t st, int *ba
     return cudaGetLastError();
 }
 
-template <int MODE>
+template <int MODE, bool PREP>
 static cudaError_t launch_solve_t(JobDev *const *jobs, int n, size_t sm, DevInfo *batch_info,
                                   double *const *sigma_out, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(k_solve<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = ensure_smem((const void *)k_solve<MODE, PREP>, sm);
     if (e != cudaSuccess) return e;
-    k_solve<MODE><<<n, kThreads, sm, st>>>(jobs, batch_info, sigma_out);
+    k_solve<MODE, PREP><<<n, kThreads, sm, st>>>(jobs, batch_info, sigma_out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_solve(JobDev *const *jobs, int n, int max_p, int mode, DevInfo *batch_info,
                          double *const *sigma_out, cudaStream_t st) {
     const size_t sm = solve_smem_bytes(max_p, mode);
-    if (mode == 1) return launch_solve_t<1>(jobs, n, sm, batch_info, sigma_out, st);
-    if (mode == 2) return launch_solve_t<2>(jobs, n, sm, batch_info, sigma_out, st);
-    return launch_solve_t<0>(jobs, n, sm, batch_info, sigma_out, st);
+    if (mode == 1) return launch_solve_t<1, false>(jobs, n, sm, batch_info, sigma_out, st);
+    if (mode == 2) return launch_solve_t<2, false>(jobs, n, sm, batch_info, sigma_out, st);
+    return launch_solve_t<0, false>(jobs, n, sm, batch_info, sigma_out, st);
+}
+
+cudaError_t launch_job(JobDev *const *jobs, int n, int max_p, int mode, DevInfo *batch_info,
+                       double *const *sigma_out, cudaStream_t st) {
+    size_t sm = solve_smem_bytes(max_p, mode);
+    if (mode == 0) {
+        const size_t b = bounds_smem_bytes(max_p);
+        sm = sm > b ? sm : b;
+    }
+    if (mode == 1) return launch_solve_t<1, true>(jobs, n, sm, batch_info, sigma_out, st);
+    if (mode == 2) return launch_solve_t<2, true>(jobs, n, sm, batch_info, sigma_out, st);
+    return launch_solve_t<0, true>(jobs, n, sm, batch_info, sigma_out, st);
 }
 
 // Psi x over all pixels: nparts CTAs write partial p x p sums into `part`
@@ -1016,7 +1079,7 @@ template <int MODE>
 static cudaError_t launch_psi_tc_t(const JobDev *job_dev, const float *wx, float2 *part, int nparts, int Q,
                                    int p, double2 *Kout, cudaStream_t st) {
     const size_t sm = tc_smem_bytes(p) + 1024;
-    cudaError_t e = cudaFuncSetAttribute(k_psi_partial_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = ensure_smem((const void *)k_psi_partial_tc<MODE>, sm);
     if (e != cudaSuccess) return e;
     int per = (Q + nparts - 1) / nparts;
     per = ((per + kTcM - 1) / kTcM) * kTcM;
@@ -1034,7 +1097,7 @@ cudaError_t launch_psi(const JobDev *job_dev, const float *wx, float2 *part, int
     if (mode == 1 && Kp == 64) return launch_psi_tc_t<1>(job_dev, wx, part, nparts, Q, p, Kout, st);
     if (mode == 2 && Kp == 64) return launch_psi_tc_t<2>(job_dev, wx, part, nparts, Q, p, Kout, st);
     const size_t sm = (size_t)p * kTile * sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(k_psi_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = ensure_smem((const void *)k_psi_partial, sm);
     if (e != cudaSuccess) return e;
     int per = (Q + nparts - 1) / nparts;
     per = ((per + kTile - 1) / kTile) * kTile;
@@ -1050,7 +1113,7 @@ template <int MODE>
 static cudaError_t launch_psi_adj_tc_t(const JobDev *job_dev, const float2 *U, double *out, int Q, int p,
                                        cudaStream_t st) {
     const size_t sm = tc_smem_bytes(p) + 1024;
-    cudaError_t e = cudaFuncSetAttribute(k_psi_adj_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = ensure_smem((const void *)k_psi_adj_tc<MODE>, sm);
     if (e != cudaSuccess) return e;
     const int ntiles = (Q + kTcM - 1) / kTcM;
     k_psi_adj_tc<MODE><<<min(ntiles, num_sms()), kThreads, sm, st>>>(job_dev, U, out);
@@ -1062,7 +1125,7 @@ cudaError_t launch_psi_adj(const JobDev *job_dev, const float2 *U, double *out, 
     if (mode == 1) return launch_psi_adj_tc_t<1>(job_dev, U, out, Q, p, st);
     if (mode == 2) return launch_psi_adj_tc_t<2>(job_dev, U, out, Q, p, st);
     const size_t sm = bounds_smem_bytes(p);
-    cudaError_t e = cudaFuncSetAttribute(k_psi_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = ensure_smem((const void *)k_psi_adj, sm);
     if (e != cudaSuccess) return e;
     const int ntiles = (Q + kTile - 1) / kTile;
     k_psi_adj<<<min(ntiles, 2 * num_sms()), kThreads, sm, st>>>(job_dev, U, out);

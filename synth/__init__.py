@@ -248,3 +248,19 @@ def custom(seed: int, p: int, n_l: int, n_m: int, n_src: int, N: int,
         sky[_distinct_pixels(Q, k, rs)] = rs.uniform(1.0, 10.0, k)
     noise_var = max(float(sky.sum()) / p * 10 ** (-snr_db / 10.0), 1e-3)
     return _finish("custom", seed, ant, l, m, 1.0, sky, noise_var, N)
+
+
+def serve_job_tc(j: int, seed: int = 6000, N: int = 10_000) -> Job:
+    """Serving mix restricted to the sizes the tensor-core path takes
+    (p in {32, 64}, grid 64x64 or 128x128), 5-50 sources, log-spiral arrays."""
+    rs = _rng(seed + j, _PICK)
+    p = int(rs.choice([32, 64]))
+    n = int(rs.choice([64, 128]))
+    ant = spiral_layout(p, 50.0, _rng(seed + j, _ARRAY))
+    l = m = grid(n)
+    sk = _rng(seed + j, _SKY)
+    n_src = int(sk.integers(5, 51))
+    sky = np.zeros(n * n)
+    sky[_distinct_pixels(n * n, n_src, sk)] = sk.lognormal(0.0, 1.0, n_src)
+    noise_var = float(sky.sum()) / p
+    return _finish("serve_tc", seed + j, ant, l, m.copy(), 1.0, sky, noise_var, N, {"job": j})
