@@ -307,6 +307,19 @@ def oracle_passes_per_image() -> float:
         return 740.0
 
 
+def profiled_traffic(B: int):
+    """DRAM bytes of one k_solve launch from the committed ncu summary (a
+    304-image launch of this workload), scaled to B images; None when absent."""
+    path = os.path.join(ROOT, "profiles", "k_solve_f16x3_bench_128x128_p64.md")
+    try:
+        for line in open(path):
+            if line.startswith("traffic_bytes_per_launch k_solve:"):
+                return float(line.split(":")[1]) * B / 304.0
+    except OSError:
+        pass
+    return None
+
+
 def cpu_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -408,7 +421,8 @@ def main():
                        "l2": "flushed between steps (512 MB write)",
                        "parallelism": f"dp{world} (independent images)"},
             "roofline": {"kernel": "k_solve", "bound": bound, "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": profiled_traffic(B) if args.precision == "f16x3" else None,
                          "peak_basis": basis},
             "solve_ms_per_step": t_solve * 1e3,
             "prepare_ms_per_step": t_prep * 1e3,
