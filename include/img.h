@@ -132,6 +132,9 @@ typedef struct {
     double cyc_lsqr;     /* ... of which in LSQR subproblems                 */
     double cyc_lsqr_fwd; /* ... of which in LSQR's forward products M v      */
     double cyc_lsqr_adj; /* ... of which in LSQR's adjoint products M^H u    */
+    double cyc_aux[6];   /* finer LSQR phases (diagnostic): forward chunks,
+                            G read-out, u update, B build, adjoint MMA wait,
+                            adjoint epilogues                               */
     double t_begin_ns;   /* device global timer when the job's CTA started   */
     double t_end_ns;     /* ... and when it finished                         */
 } img_solve_info;

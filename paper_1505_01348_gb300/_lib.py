@@ -46,10 +46,13 @@ class SolveInfo(C.Structure):
                 ("lambda_min", C.c_double), ("op_flops", C.c_double),
                 ("cyc_total", C.c_double), ("cyc_gradient", C.c_double),
                 ("cyc_lsqr", C.c_double), ("cyc_lsqr_fwd", C.c_double),
-                ("cyc_lsqr_adj", C.c_double), ("t_begin_ns", C.c_double), ("t_end_ns", C.c_double)]
+                ("cyc_lsqr_adj", C.c_double), ("cyc_aux", C.c_double * 6),
+                ("t_begin_ns", C.c_double), ("t_end_ns", C.c_double)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["cyc_aux"] = list(self.cyc_aux)
+        return d
 
 
 class ServerParams(C.Structure):

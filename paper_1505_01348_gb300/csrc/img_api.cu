@@ -210,6 +210,7 @@ void fill_info(img_solve_info *o, const DevInfo &d) {
     o->cyc_lsqr = d.cyc_lsqr;
     o->cyc_lsqr_fwd = d.cyc_lsqr_fwd;
     o->cyc_lsqr_adj = d.cyc_lsqr_adj;
+    for (int k = 0; k < 6; ++k) o->cyc_aux[k] = d.cyc_aux[k];
     o->t_begin_ns = (double)d.t_begin_ns;
     o->t_end_ns = (double)d.t_end_ns;
 }

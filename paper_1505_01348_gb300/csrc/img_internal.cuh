@@ -23,6 +23,7 @@ struct DevInfo {
     double cyc_lsqr;
     double cyc_lsqr_fwd;
     double cyc_lsqr_adj;
+    double cyc_aux[6];
     unsigned long long t_begin_ns;   // device global timer at the job's start and end
     unsigned long long t_end_ns;
 };

@@ -436,34 +436,50 @@ template <int MODE>
 __device__ int lsqr_cta(const JobDev &J, int f, float2 *A, TcWork &T, SolveShared &S, DevInfo &info) {
     constexpr bool BF = MODE == 2;
     const int p = J.p, pp = p * p;
-    const int *fpos = J.fpos;
+    const int *__restrict__ fpos = J.fpos;
+    float2 *__restrict__ t = J.W0;
     // free-set tiles resident in shared memory for the whole solve (tensor
-    // cores, Kp = 64, at most two 128-pixel tiles)
+    // cores, Kp = 64, at most two 128-pixel tiles); the f-vectors then live
+    // in shared memory too
     bool resident = false;
     float sXr = 1.f;
     unsigned char *stage = nullptr;
+    float *v = J.v, *w = J.w, *xs = J.xs, *sF = J.sF, *wt = J.xs + J.cap;
     if constexpr (MODE != 0) {
         resident = T.Kp == 64 && f <= 2 * kTcM;
         if (resident) {
             stage = T.Blo + (T.Blo - T.Bhi);
+            float *fv = reinterpret_cast<float *>(stage + tc_stage_bytes(p));
+            v = fv;
+            w = fv + 2 * kTcM;
+            xs = fv + 4 * kTcM;
+            sF = fv + 6 * kTcM;
+            wt = fv + 8 * kTcM;
             sXr = list_scale(J, fpos, f, S.dbuf);
             tc_gen_X_cache<BF>(J, T, 0, fpos, 0, min(kTcM, f), sXr);
             if (f > kTcM) tc_gen_X_cache<BF>(J, T, 1, fpos, kTcM, f - kTcM, sXr);
         }
     }
-    for (int j = threadIdx.x; j < f; j += blockDim.x) J.sF[j] = J.scale[J.supp[fpos[j]]];
-    float2 *t = J.W0;
-    double acc = 0.0;
-    for (int e = threadIdx.x; e < pp; e += blockDim.x) acc += (double)t[e].x * t[e].x + (double)t[e].y * t[e].y;
-    double beta = sqrt(block_sum(acc, S.dbuf));
+    {
+        const int *__restrict__ supp = J.supp;
+        const float *__restrict__ scale = J.scale;
+        for (int j = threadIdx.x; j < f; j += blockDim.x) sF[j] = scale[supp[fpos[j]]];
+    }
+    float acc = 0.f;     // per-thread partial (<= 16 terms), reduced in FP64
+    for (int e = threadIdx.x; e < pp; e += blockDim.x) acc = fmaf(t[e].x, t[e].x, fmaf(t[e].y, t[e].y, acc));
+    double beta = sqrt(block_sum((double)acc, S.dbuf));
     const double bnorm = beta;
-    for (int j = threadIdx.x; j < f; j += blockDim.x) J.xs[j] = 0.f;
-    if (beta == 0.0) { __syncthreads(); return 0; }
+    for (int j = threadIdx.x; j < f; j += blockDim.x) xs[j] = 0.f;
+    if (beta == 0.0) {
+        for (int j = threadIdx.x; j < f; j += blockDim.x) J.xs[j] = 0.f;
+        __syncthreads();
+        return 0;
+    }
     double us = 1.0 / beta;
     auto adjoint = [&](auto epi) {
         if constexpr (MODE != 0) {
             if (resident) {
-                tc_adjoint_resident<BF>(T, t, p, f, sXr, S.red, S.dbuf, epi);
+                tc_adjoint_resident<BF>(T, t, p, f, sXr, S.red, S.dbuf, epi, info.cyc_aux);
                 return;
             }
         }
@@ -471,73 +487,77 @@ __device__ int lsqr_cta(const JobDev &J, int f, float2 *A, TcWork &T, SolveShare
     };
     {
         const float fus = (float)us;
-        adjoint([&](int j, float y) { J.v[j] = J.sF[j] * (y * fus); });
+        adjoint([&](int j, float y) { v[j] = sF[j] * (y * fus); });
     }
-    acc = 0.0;
-    for (int j = threadIdx.x; j < f; j += blockDim.x) acc += (double)J.v[j] * J.v[j];
-    double alpha = sqrt(block_sum(acc, S.dbuf));
-    if (alpha == 0.0) return 0;
+    acc = 0.f;
+    for (int j = threadIdx.x; j < f; j += blockDim.x) acc = fmaf(v[j], v[j], acc);
+    double alpha = sqrt(block_sum((double)acc, S.dbuf));
+    int it = 0;
+    if (alpha == 0.0) {
+        for (int j = threadIdx.x; j < f; j += blockDim.x) J.xs[j] = 0.f;
+        __syncthreads();
+        return 0;
+    }
     {
         const float ia = (float)(1.0 / alpha);
         for (int j = threadIdx.x; j < f; j += blockDim.x) {
-            J.v[j] *= ia;
-            J.w[j] = J.v[j];
+            v[j] *= ia;
+            w[j] = v[j];
         }
     }
     __syncthreads();
     double phibar = beta, rhobar = alpha, anorm2 = 0.0;
     const int maxit = J.lsqr_maxit > 0 ? J.lsqr_maxit : 4 * f + 20;
-    int it = 0;
-    float *wt = J.xs + J.cap;   // weight scratch (cap floats after xs)
+    const double atol = J.lsqr_atol, btol = J.lsqr_btol;
     for (it = 1; it <= maxit; ++it) {
         // t <- M v - alpha u  (u = t * us), beta = ||t||
-        for (int j = threadIdx.x; j < f; j += blockDim.x) wt[j] = J.sF[j] * J.v[j];
+        for (int j = threadIdx.x; j < f; j += blockDim.x) wt[j] = sF[j] * v[j];
         __syncthreads();
         long long tc0 = clock64();
         const float fa = (float)(alpha * us);
-        acc = 0.0;
+        acc = 0.f;
         bool done = false;
         if constexpr (MODE != 0) {
             if (resident) {
                 float inv;
-                const float *G = tc_forward_resident<BF>(T, stage, f, wt, sXr, &inv, S.dbuf);
+                const float *G = tc_forward_resident<BF>(T, stage, f, wt, sXr, &inv, S.dbuf, info.cyc_aux);
+                const long long cu = clock64();
                 for (int e = threadIdx.x; e < pp; e += blockDim.x) {
                     const int bcol = e / p, a = e - bcol * p;
                     float2 kv = G ? tc_k_entry(G, T.Kp, a, bcol) : make_float2(0.f, 0.f);
-                    const float2 tn = make_float2(kv.x * inv - fa * t[e].x, kv.y * inv - fa * t[e].y);
+                    const float2 to = t[e];
+                    const float2 tn = make_float2(kv.x * inv - fa * to.x, kv.y * inv - fa * to.y);
                     t[e] = tn;
-                    acc += (double)tn.x * tn.x + (double)tn.y * tn.y;
+                    acc = fmaf(tn.x, tn.x, fmaf(tn.y, tn.y, acc));
                 }
+                info.cyc_aux[2] += (double)(clock64() - cu);
                 done = true;
             }
         }
         if (!done) {
             forward_cache<MODE>(J, T, fpos, wt, f, nullptr, false, J.W1, A, S.wsm, S.dbuf);
+            const float2 *__restrict__ W1 = J.W1;
             for (int e = threadIdx.x; e < pp; e += blockDim.x) {
-                const float2 mv = J.W1[e];
-                const float2 tn = make_float2(mv.x - fa * t[e].x, mv.y - fa * t[e].y);
+                const float2 mv = W1[e];
+                const float2 to = t[e];
+                const float2 tn = make_float2(mv.x - fa * to.x, mv.y - fa * to.y);
                 t[e] = tn;
-                acc += (double)tn.x * tn.x + (double)tn.y * tn.y;
+                acc = fmaf(tn.x, tn.x, fmaf(tn.y, tn.y, acc));
             }
         }
         info.cyc_lsqr_fwd += (double)(clock64() - tc0);
-        beta = sqrt(block_sum(acc, S.dbuf));
+        beta = sqrt(block_sum((double)acc, S.dbuf));
         us = beta > 0.0 ? 1.0 / beta : 0.0;
         anorm2 += alpha * alpha + beta * beta;
         // v <- M^H u - beta v
         const float fb = (float)beta, fus = (float)us;
         tc0 = clock64();
-        adjoint([&](int j, float y) { J.v[j] = J.sF[j] * (y * fus) - fb * J.v[j]; });
+        adjoint([&](int j, float y) { v[j] = sF[j] * (y * fus) - fb * v[j]; });
         info.cyc_lsqr_adj += (double)(clock64() - tc0);
-        acc = 0.0;
-        for (int j = threadIdx.x; j < f; j += blockDim.x) acc += (double)J.v[j] * J.v[j];
-        alpha = sqrt(block_sum(acc, S.dbuf));
-        if (alpha > 0.0) {
-            const float ia = (float)(1.0 / alpha);
-            for (int j = threadIdx.x; j < f; j += blockDim.x) J.v[j] *= ia;
-        }
-        __syncthreads();
-        // plane rotation
+        acc = 0.f;
+        for (int j = threadIdx.x; j < f; j += blockDim.x) acc = fmaf(v[j], v[j], acc);
+        alpha = sqrt(block_sum((double)acc, S.dbuf));
+        // plane rotation (scalars in FP64, the same in every thread)
         const double rho = hypot(rhobar, beta);
         const double c = rhobar / rho, s = beta / rho;
         const double theta = s * alpha;
@@ -545,20 +565,26 @@ __device__ int lsqr_cta(const JobDev &J, int f, float2 *A, TcWork &T, SolveShare
         const double phi = c * phibar;
         phibar = s * phibar;
         const float t1 = (float)(phi / rho), t2 = (float)(-theta / rho);
-        acc = 0.0;
+        const float ia = alpha > 0.0 ? (float)(1.0 / alpha) : 1.f;
+        acc = 0.f;
         for (int j = threadIdx.x; j < f; j += blockDim.x) {
-            const float xj = J.xs[j] + t1 * J.w[j];
-            J.xs[j] = xj;
-            J.w[j] = J.v[j] + t2 * J.w[j];
-            acc += (double)xj * xj;
+            const float vj = v[j] * ia;                 // v <- v / alpha
+            v[j] = vj;
+            const float xj = xs[j] + t1 * w[j];
+            xs[j] = xj;
+            w[j] = vj + t2 * w[j];
+            acc = fmaf(xj, xj, acc);
         }
-        const double xnorm = sqrt(block_sum(acc, S.dbuf));
+        const double xnorm = sqrt(block_sum((double)acc, S.dbuf));
         const double rnorm = phibar;
         const double arnorm = phibar * alpha * fabs(c);
         const double anorm = sqrt(anorm2);
-        if (rnorm <= J.lsqr_btol * bnorm + J.lsqr_atol * anorm * xnorm) break;
-        if (arnorm <= J.lsqr_atol * anorm * rnorm) break;
+        if (rnorm <= btol * bnorm + atol * anorm * xnorm) break;
+        if (arnorm <= atol * anorm * rnorm) break;
     }
+    if (xs != J.xs)
+        for (int j = threadIdx.x; j < f; j += blockDim.x) J.xs[j] = xs[j];
+    __syncthreads();
     return min(it, maxit);
 }
 
@@ -715,18 +741,27 @@ k_solve(JobDev *const *jobs, DevInfo *batch_info, double *const *sigma_out) {
                 const long long tg = clock64();
                 double best = INFINITY;
                 int bidx = 0x7fffffff;
-                adjoint_full<MODE>(J, Ug, A, T, S.red, S.dbuf, [&](int i, float val) {
-                    const float g = -J.scale[i] * val;
-                    J.grad[i] = g;
-                    const unsigned char st = J.set[i];
-                    if (st != IMG_SET_F) {
-                        const double lam = st == IMG_SET_U ? -(double)g : (double)g;
-                        if (lam < -(double)J.eps[i] && (lam < best || (lam == best && i < bidx))) {
-                            best = lam;
-                            bidx = i;
+                float bestf = INFINITY;
+                {
+                    const float *__restrict__ scale = J.scale;
+                    const float *__restrict__ eps = J.eps;
+                    const unsigned char *__restrict__ set = J.set;
+                    float *__restrict__ grad = J.grad;
+                    adjoint_full<MODE>(J, Ug, A, T, S.red, S.dbuf, [&](int i, float val) {
+                        // lambda_L = g, lambda_U = -g (eq. etaL, eq. etaU); g and eps are FP32
+                        const float g = -scale[i] * val;
+                        grad[i] = g;
+                        const unsigned char st = set[i];
+                        if (st != IMG_SET_F) {
+                            const float lam = st == IMG_SET_U ? -g : g;
+                            if (lam < -eps[i] && (lam < bestf || (lam == bestf && i < bidx))) {
+                                bestf = lam;
+                                bidx = i;
+                            }
                         }
-                    }
-                });
+                    });
+                }
+                best = bestf;
                 info.op_flops += flops_adj(p, Q);
                 block_argmin(best, bidx, S.vbuf, S.ibuf);
                 info.cyc_gradient += (double)(clock64() - tg);
@@ -967,7 +1002,8 @@ __global__ void k_d2f(const double *src, float *dst, int n) {
 // ---------------------------------------------------------------- launchers
 size_t solve_smem_bytes(int p, int mode) {
     size_t b = (size_t)p * kTile * sizeof(float2);
-    const size_t tc = tc_smem_bytes(p) + tc_stage_bytes(p);
+    // tensor tiles + forward staging + five LSQR f-vectors of 256 floats
+    const size_t tc = tc_smem_bytes(p) + tc_stage_bytes(p) + 10 * kTcM * sizeof(float);
     if (mode != 0) b = b > tc ? b : tc;
     return b + 1024;
 }

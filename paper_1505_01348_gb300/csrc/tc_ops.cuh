@@ -800,7 +800,8 @@ __device__ inline void tc_issue_fwd_chunk(const TcWork &T, const unsigned char *
 // that read it completed.  Returns G (scaled by sX^2 sW; *scale = 1/that).
 template <bool BF16>
 __device__ const float *tc_forward_resident(TcWork &T, unsigned char *stage, int f, const float *w,
-                                            float sX, float *scale, double *dbuf) {
+                                            float sX, float *scale, double *dbuf, double *cyc = nullptr) {
+    long long c0 = clock64();
     const float sW = pow2_scale_of(w, f, dbuf);
     const uint32_t idesc = idesc_f16_mn(2 * T.Kp, BF16 ? 1 : 0);
     const int nchunks = (f + kChunk - 1) / kChunk;
@@ -825,14 +826,21 @@ __device__ const float *tc_forward_resident(TcWork &T, unsigned char *stage, int
     }
     tc_fence_after();
     __syncthreads();
+    long long c1 = clock64();
     *scale = 1.f / (sX * sX * sW);
-    return nchunks ? tc_read_fwd(T, reinterpret_cast<float *>(T.Bhi)) : nullptr;
+    const float *G = nchunks ? tc_read_fwd(T, reinterpret_cast<float *>(T.Bhi)) : nullptr;
+    if (cyc) {
+        cyc[0] += (double)(c1 - c0);
+        cyc[1] += (double)(clock64() - c1);
+    }
+    return G;
 }
 
 // Adjoint over the resident tiles: epi(j, Re(c_j^H U c_j)) for j < f.
 template <bool BF16, class Epi>
 __device__ void tc_adjoint_resident(TcWork &T, const float2 *U, int p, int f, float sX, float *red,
-                                    double *dbuf, Epi epi) {
+                                    double *dbuf, Epi epi, double *cyc = nullptr) {
+    long long c0 = clock64();
     const float sB = tc_build_B<BF16>(U, p, T, dbuf);
     const uint32_t idesc = idesc_f16(2 * T.Kp, BF16 ? 1 : 0);
     const int ntiles = (f + kTcM - 1) / kTcM;
@@ -841,15 +849,25 @@ __device__ void tc_adjoint_resident(TcWork &T, const float2 *U, int p, int f, fl
     if (threadIdx.x == 0)
         for (int t = 0; t < ntiles; ++t) tc_issue(T, t, idesc);
     const float inv = 1.f / (sX * sX * sB);
+    long long c1 = clock64(), cw = 0, ce = 0;
     for (int t = 0; t < ntiles; ++t) {
+        long long a0 = clock64();
         if (!mbar_wait(&T.bar[t], T.phase[t])) T.timeouts++;
         T.phase[t] ^= 1u;
         tc_fence_after();
         __syncthreads();
+        long long a1 = clock64();
         tc_epilogue<BF16>(T, t, red);
         const int j = t * kTcM + threadIdx.x;
         if (threadIdx.x < kTcM && j < f) epi(j, red[threadIdx.x] * inv);
         __syncthreads();
+        cw += a1 - a0;
+        ce += clock64() - a1;
+    }
+    if (cyc) {
+        cyc[3] += (double)(c1 - c0);
+        cyc[4] += (double)cw;
+        cyc[5] += (double)ce;
     }
 }
 
