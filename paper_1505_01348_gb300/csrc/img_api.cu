@@ -9,6 +9,7 @@
 
 #include "../../include/img.h"
 #include "img_internal.cuh"
+#include "tc_wide.cuh"
 
 using img::DevInfo;
 using img::JobDev;
@@ -106,6 +107,8 @@ size_t carve(img_ctx *c, char *base) {
     J.ev = cv.take<int>(J.ev_cap);
     J.evv = cv.take<float>(J.ev_cap);
     J.ev_count = cv.take<int>(1);
+    J.Bimg = (p > img::kMaxTcP && p <= img::kMaxWideP) ? cv.take<unsigned char>(2 * img::wide_B_bytes(p)) : nullptr;
+    J.Bscale = cv.take<float>(2);
     J.info = cv.take<DevInfo>(1);
     J.flags = cv.take<int>(4);
     c->dj = cv.take<JobDev>(1);
@@ -118,10 +121,16 @@ size_t carve(img_ctx *c, char *base) {
     return cv.off + 256;
 }
 
-// Arithmetic of the adjoint for one context: tensor cores when requested and
+// Arithmetic of the solver for one context: tensor cores when requested and
 // the 2p x 2p operand tiles fit in shared memory, CUDA cores otherwise.
 int mode_of(const img_ctx *c) {
     return (c->prm.precision != IMG_PREC_FP32 && c->prm.p <= img::kMaxTcP) ? c->prm.precision : 0;
+}
+
+// Arithmetic of the stand-alone adjoint (dirty image, bounds, Psi^H): tensor
+// cores up to p = 256 (streamed operand above p = 64).
+int op_mode_of(const img_ctx *c) {
+    return (c->prm.precision != IMG_PREC_FP32 && c->prm.p <= img::kMaxWideP) ? c->prm.precision : 0;
 }
 
 bool finite_all(const double *v, size_t n) {
@@ -138,7 +147,7 @@ img_status prepare(img_ctx *c) {
     if (c->prepared) return (img_status)c->prep_status;
     CK(img::launch_factor(c->djp, 1, c->stream));
     const int ntiles = (c->hj.Q + img::kTile - 1) / img::kTile;
-    CK(img::launch_bounds(c->djp, 1, ntiles, c->prm.p, mode_of(c), c->stream));
+    CK(img::launch_bounds(c->djp, 1, ntiles, c->prm.p, op_mode_of(c), c->stream));
     CK(img::launch_finalize(c->djp, 1, c->stream, nullptr));
     int flag = 0;
     CK(cudaMemcpyAsync(&flag, c->hj.flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -479,7 +488,7 @@ img_status img_psi_adj(img_ctx *c, const double *U, double *out, int on_device) 
     CK(cudaMemcpyAsync(c->Z, U, (size_t)p * p * sizeof(double2),
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     CK(img::launch_z2c(c->Z, c->U32, p * p, c->stream));
-    CK(img::launch_psi_adj(c->dj, c->U32, on_device ? out : c->outd, Q, p, mode_of(c), c->stream));
+    CK(img::launch_psi_adj(c->dj, c->U32, on_device ? out : c->outd, Q, p, op_mode_of(c), c->stream));
     if (on_device) return sync(c);
     return copy_out_double(c, c->outd, out, Q, 0);
 }
@@ -489,19 +498,30 @@ img_status img_psi_adj(img_ctx *c, const double *U, double *out, int on_device) 
 namespace {
 
 // Jobs of a batch grouped by operator arithmetic (one launch per group):
-// order[] lists job indices group by group; groups[m] = [begin, end).
+// order[] lists job indices group by group; groups[k] = [begin, end).
+// Keys 0..2: solver and bounds in arithmetic k (FP32, F16X3, BF16X3, the
+// latter two for p <= 64); keys 3, 4: bounds on the streamed tensor-core
+// operator in F16X3 / BF16X3 (64 < p <= 256), solver on CUDA cores.
+constexpr int kGroups = 5;
 struct Groups {
     std::vector<int> order;
-    int begin[3] = {0, 0, 0}, end[3] = {0, 0, 0};
-    int max_p[3] = {0, 0, 0}, max_tiles[3] = {1, 1, 1};
+    int begin[kGroups] = {}, end[kGroups] = {};
+    int max_p[kGroups] = {}, max_tiles[kGroups] = {1, 1, 1, 1, 1};
+    static int solve_mode(int k) { return k <= 2 ? k : 0; }
+    static int bounds_mode(int k) { return k <= 2 ? k : k - 2; }
 };
+
+int group_key(const img_ctx *c) {
+    const int m = mode_of(c), om = op_mode_of(c);
+    return (m == 0 && om != 0) ? om + 2 : m;
+}
 
 Groups group_by_mode(img_ctx *const *ctxs, int n) {
     Groups g;
-    for (int m = 0; m < 3; ++m) {
+    for (int m = 0; m < kGroups; ++m) {
         g.begin[m] = (int)g.order.size();
         for (int j = 0; j < n; ++j) {
-            if (mode_of(ctxs[j]) != m) continue;
+            if (group_key(ctxs[j]) != m) continue;
             g.order.push_back(j);
             g.max_p[m] = std::max(g.max_p[m], ctxs[j]->prm.p);
             g.max_tiles[m] = std::max(g.max_tiles[m], (ctxs[j]->hj.Q + img::kTile - 1) / img::kTile);
@@ -523,12 +543,12 @@ img_status check_batch(img_ctx *const *ctxs, int n) {
 // Factor + bounds of the listed jobs (device pointer array already in
 // g_ws.jobs in group order), one launch per kernel and group.
 img_status launch_prepare(const Groups &g, cudaStream_t s, int *status_out) {
-    for (int m = 0; m < 3; ++m) {
+    for (int m = 0; m < kGroups; ++m) {
         const int nb = g.end[m] - g.begin[m];
         if (!nb) continue;
         JobDev *const *jp = g_ws.jobs + g.begin[m];
         CK(img::launch_factor(jp, nb, s));
-        CK(img::launch_bounds(jp, nb, g.max_tiles[m], g.max_p[m], m, s));
+        CK(img::launch_bounds(jp, nb, g.max_tiles[m], g.max_p[m], Groups::bounds_mode(m), s));
         CK(img::launch_finalize(jp, nb, s, status_out ? status_out + g.begin[m] : nullptr));
     }
     return IMG_OK;
@@ -597,10 +617,10 @@ img_status img_solve_batch(img_ctx *const *ctxs, int n, double *const *sigma, im
     }
     if (on_device)
         CK(cudaMemcpyAsync(g_ws.sig, outs.data(), n * sizeof(double *), cudaMemcpyHostToDevice, s));
-    for (int m = 0; m < 3; ++m) {
+    for (int m = 0; m < kGroups; ++m) {
         const int nb = g.end[m] - g.begin[m];
         if (!nb) continue;
-        CK(img::launch_solve(g_ws.jobs + g.begin[m], nb, g.max_p[m], m, g_ws.infos + g.begin[m],
+        CK(img::launch_solve(g_ws.jobs + g.begin[m], nb, g.max_p[m], Groups::solve_mode(m), g_ws.infos + g.begin[m],
                              on_device ? g_ws.sig + g.begin[m] : nullptr, s));
     }
     std::vector<DevInfo> d(n);
@@ -833,11 +853,23 @@ struct img_server {
         for (int q = 0; q < n; ++q) ptrs[q] = ctxs[g.order[q]]->dj;
         CK(cudaMemcpyAsync(sl.jobs, sl.stage(ptrs.data(), n * sizeof(JobDev *)), n * sizeof(JobDev *),
                            cudaMemcpyHostToDevice, sl.s));
-        for (int md = 0; md < 3; ++md) {
+        for (int md = 0; md < kGroups; ++md) {
             const int nb = g.end[md] - g.begin[md];
             if (!nb) continue;
             JobDev *const *jp = sl.jobs + g.begin[md];
-            CK(img::launch_job(jp, nb, g.max_p[md], md, sl.infos + g.begin[md], nullptr, sl.s));
+            if (md <= 2) {
+                // one fused kernel: tables, factor, bounds and solve in one CTA per job
+                CK(img::launch_job(jp, nb, g.max_p[md], md, sl.infos + g.begin[md], nullptr, sl.s));
+            } else {
+                // wide arrays: bounds on the streamed tensor-core operator, as the
+                // single-job API computes them, then the solver
+                CK(img::launch_tables(jp, nb, sl.s));
+                CK(img::launch_factor(jp, nb, sl.s));
+                CK(img::launch_bounds(jp, nb, g.max_tiles[md], g.max_p[md], Groups::bounds_mode(md), sl.s));
+                CK(img::launch_finalize(jp, nb, sl.s, nullptr));
+                CK(img::launch_solve(jp, nb, g.max_p[md], Groups::solve_mode(md), sl.infos + g.begin[md], nullptr,
+                                     sl.s));
+            }
         }
         CK(cudaMemcpyAsync(sl.h_infos, sl.infos, n * sizeof(DevInfo), cudaMemcpyDeviceToHost, sl.s));
         // results in group order: remember the permutation

@@ -72,6 +72,10 @@ struct JobDev {
     float *v, *w, *xs;     // cap, LSQR vectors indexed by F position
     float *sF;             // cap, s_i of the free pixels in F order (per LSQR solve)
     float2 *W0, *W1, *W2;  // p*p scratch matrices
+    // chunked B images of R_hat and R_hat^-1 for the wide tensor-core
+    // operators (64 < p <= 256), and their scales
+    unsigned char *Bimg;
+    float *Bscale;
     // decision log (Table I order): kind << 24 | pixel, and lambda or mu
     int *ev;
     float *evv;
@@ -86,6 +90,8 @@ struct JobDev {
 // `jobs` is a device array of n job pointers.
 cudaError_t launch_tables(JobDev *const *jobs, int n, cudaStream_t st);
 cudaError_t launch_factor(JobDev *const *jobs, int n, cudaStream_t st);
+// mode 1/2 use tensor cores: the shared-memory operator for p <= 64, the
+// streamed (wide) operator for 64 < p <= 256.
 cudaError_t launch_bounds(JobDev *const *jobs, int n, int max_tiles, int max_p, int mode,
                           cudaStream_t st);
 cudaError_t launch_finalize(JobDev *const *jobs, int n, cudaStream_t st, int *batch_status);
@@ -105,7 +111,8 @@ cudaError_t launch_d2f(const double *src, float *dst, int n, cudaStream_t st);
 cudaError_t launch_to_double(const float *src, double *dst, int n, cudaStream_t st);
 
 size_t solve_smem_bytes(int p, int mode);
-constexpr int kMaxTcP = 64;   // tensor-core operators need 2p x 2p tiles in shared memory
+constexpr int kMaxTcP = 64;   // tensor-core solver: 2p x 2p operand tiles in shared memory
+constexpr int kMaxWideP = 256; // streamed tensor-core operators (bounds, Psi^H)
 size_t bounds_smem_bytes(int p);
 
 }  // namespace img
