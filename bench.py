@@ -227,6 +227,53 @@ def run_ours(args, rank: int, world: int):
 
 
 # ---------------------------------------------------------------- serving
+def run_operators(args, ps=(128, 256), n: int = 256, reps: int = 20):
+    """Adjoint operator Psi^H (Eq. 16) on wide arrays, full 256x256 grid:
+    the streamed tensor-core kernel (64 < p <= 256).  Each call copies U,
+    converts it, writes the chunked operand image and runs the adjoint; calls
+    are queued back to back on one stream and timed with CUDA events.
+    Useful flops: 8 p^2 Q; issued: the three split products on the padded
+    2Kp x 2Kp operand, 3 * 2 * 128 * (2Kp)^2 per 128-pixel tile."""
+    import torch
+    import paper_1505_01348_gb300 as G
+    import synth
+
+    prec = PRECISIONS[args.precision]
+    if prec == 0:
+        return None
+    pk = measured_peaks()
+    peak = float(pk.get("bf16_tflops") or 1900.0)
+    out_d = {"kernel": "k_psi_adj_wide", "grid": f"{n}x{n}", "precision": args.precision,
+             "per_call": "U copy + FP32 conversion + operand image + adjoint", "peak_tflops": peak,
+             "peak_basis": "measured dense BF16 burst (FP16 runs at the BF16 rate)"}
+    st = torch.cuda.Stream()
+    for p in ps:
+        job = synth.custom(7000 + p, p, n, n, 20, 10_000, radius=50.0)
+        # the context works on this stream, so events recorded on it bracket the calls
+        im = G.Imager.from_job(job, precision=prec, stream=st.cuda_stream)
+        U = torch.tensor(np.asfortranarray(job.R).T.copy(), dtype=torch.complex128, device="cuda")
+        out = torch.empty(job.Q, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            im.psi_adj(U, out)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            im.psi_adj(U, out, wait=False)
+        e1.record(st)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3 / reps
+        im.close()
+        kp = (p + 31) // 32 * 32
+        tiles = ((n + 7) // 8) * ((n + 15) // 16)
+        useful = 8.0 * p * p * job.Q
+        issued = 3 * 2.0 * 128 * (2 * kp) ** 2 * tiles
+        out_d[f"p{p}"] = {"us_per_call": t * 1e6, "useful_tflops": useful / t / 1e12,
+                          "issued_tflops": issued / t / 1e12, "issued_frac": issued / t / 1e12 / peak}
+    return out_d
+
+
 def run_serve(args, rate: float = 200.0, seconds: float = 10.0, distinct: int = 48):
     """Poisson arrivals of mixed jobs into the continuous-batching server;
     latencies are the server's submit-to-done times."""
@@ -373,6 +420,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-ops", action="store_true")
+    ap.add_argument("--ops-only", action="store_true",
+                    help="only the wide-array adjoint measurement (one JSON line)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -383,6 +433,12 @@ def main():
             run_reference(args)
         return
     import torch
+    if args.ops_only:
+        if rank == 0:
+            import paper_1505_01348_gb300 as G
+            G.load()
+            print(json.dumps({"operators": run_operators(args)}), flush=True)
+        return
     if world > 1:
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         torch.distributed.init_process_group("nccl")
@@ -432,6 +488,8 @@ def main():
             "clocks": r["clocks"],
             "e2e": r["e2e"],
         }
+        if not args.no_ops and world == 1:
+            line["operators"] = run_operators(args)
         if not args.no_serve and world == 1:
             line["serve"] = run_serve(args)
         if not args.no_cpu and world == 1:

@@ -201,7 +201,12 @@ img_status img_get_events(img_ctx *ctx, int *events, double *values, int capacit
 img_status img_psi(img_ctx *ctx, const double *x, double *Kout, int on_device);
 
 /* Adjoint operator (Psi^H vect(U))_i = Re(a_i^H U a_i) (Sec. V-B):
- * U p x p Hermitian complex128 column-major -> out[0..Q) double. */
+ * U p x p Hermitian complex128 column-major -> out[0..Q) double.
+ * Tensor-core arithmetic (IMG_PREC_F16X3 / BF16X3) up to p = 256; above
+ * p = 64 the operand streams from global memory.
+ * img_psi and img_psi_adj also take on_device = 2: device pointers, work
+ * queued on the context's stream and the call returns without waiting
+ * (the caller orders or synchronises with that stream). */
 img_status img_psi_adj(img_ctx *ctx, const double *U, double *out, int on_device);
 
 /* Factor R_hat, dirty images and bounds of several jobs in single launches

@@ -263,26 +263,28 @@ class Imager:
                "img_get_events")
         return [(int(e) >> 24, int(e) & 0xFFFFFF, float(v)) for e, v in zip(ev, val)]
 
-    def psi(self, x, out=None):
+    def psi(self, x, out=None, wait=True):
         """K = unvect(Psi x) (p x p, column-major).  Host arrays, or CUDA
-        tensors (float64 x, complex128 out) that stay on the device."""
+        tensors (float64 x, complex128 out) that stay on the device; with
+        wait=False a device call returns once queued on the context stream."""
         if _is_device(x):
             if out is None:
                 raise ValueError("device input needs a device output")
-            _check(self._lib.img_psi(self.h, _ptr(x), _ptr(out), 1), "img_psi")
+            _check(self._lib.img_psi(self.h, _ptr(x), _ptr(out), 1 if wait else 2), "img_psi")
             return out
         x = np.ascontiguousarray(x, dtype=np.float64)
         K = np.empty((self.p, self.p), dtype=np.complex128, order="F")
         _check(self._lib.img_psi(self.h, x.ctypes.data, K.ctypes.data, 0), "img_psi")
         return K
 
-    def psi_adj(self, U, out=None):
+    def psi_adj(self, U, out=None, wait=True):
         """Re(a_i^H U a_i) for every pixel.  Host arrays, or CUDA tensors
-        (complex128 U column-major, float64 out) that stay on the device."""
+        (complex128 U column-major, float64 out) that stay on the device; with
+        wait=False a device call returns once queued on the context stream."""
         if _is_device(U):
             if out is None:
                 raise ValueError("device input needs a device output")
-            _check(self._lib.img_psi_adj(self.h, _ptr(U), _ptr(out), 1), "img_psi_adj")
+            _check(self._lib.img_psi_adj(self.h, _ptr(U), _ptr(out), 1 if wait else 2), "img_psi_adj")
             return out
         U = np.asfortranarray(U, dtype=np.complex128)
         out = np.empty(self.Q, dtype=np.float64)

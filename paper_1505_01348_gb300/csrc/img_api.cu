@@ -479,6 +479,7 @@ img_status img_psi(img_ctx *c, const double *x, double *Kout, int on_device) {
     CK(img::launch_psi(c->dj, c->wx, c->part, c->nparts, Q, p, mode_of(c), c->Z, c->stream));
     CK(cudaMemcpyAsync(Kout, c->Z, (size_t)p * p * sizeof(double2),
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    if (on_device == 2) return IMG_OK;           // stream-ordered, no host wait
     return sync(c);
 }
 
@@ -489,6 +490,7 @@ img_status img_psi_adj(img_ctx *c, const double *U, double *out, int on_device) 
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     CK(img::launch_z2c(c->Z, c->U32, p * p, c->stream));
     CK(img::launch_psi_adj(c->dj, c->U32, on_device ? out : c->outd, Q, p, op_mode_of(c), c->stream));
+    if (on_device == 2) return IMG_OK;           // stream-ordered, no host wait
     if (on_device) return sync(c);
     return copy_out_double(c, c->outd, out, Q, 0);
 }

@@ -229,61 +229,59 @@ __global__ void __launch_bounds__(kThreads, 1) k_psi_adj_tc(const JobDev *Jp, co
     tc_teardown(T, J.p);
 }
 
-// Chunked B images of R_hat (blockIdx.y = 0) and R_hat^-1 (1) per job.
+// Chunked B images of R_hat (blockIdx.y = 0) and R_hat^-1 (1) per job; one
+// CTA per (64-column chunk, block of kEmbRows rows): blockIdx.z = chunk *
+// (512 / kEmbRows) + row block.
 template <int MODE>
 __global__ void k_emb_bounds(JobDev *const *jobs) {
     const JobDev &J = *jobs[blockIdx.x];
-    if (J.flags[0] != 0) return;
+    constexpr int kRB = 2 * kWideMaxP / kEmbRows;
+    const int kc = blockIdx.z / kRB, rb = blockIdx.z - kc * kRB;
+    if (J.flags[0] != 0 || kc >= wide_nk(J.p) || rb * kEmbRows >= 2 * wide_kp(J.p)) return;
     const int w = blockIdx.y;
-    emb_B_cta<MODE == 2>(w ? J.Ri32 : J.R32, J.p, J.Bimg + (size_t)w * wide_B_bytes(J.p), J.Bscale + w);
+    emb_B_chunk<MODE == 2>(w ? J.Ri32 : J.R32, J.p, J.Bimg + (size_t)w * wide_B_bytes(J.p), J.Bscale + w, kc,
+                           rb);
 }
 
-// Wide tensor-core k_bounds: dirty image and a^H R^-1 a for 64 < p <= 256.
+// Wide tensor-core bounds for 64 < p <= 256: dirty image (B = R_hat) and
+// a^H R^-1 a (B = R_hat^-1) in one warp-specialised pass over the tiles.
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, 1) k_bounds_wide(JobDev *const *jobs) {
+__global__ void __launch_bounds__(kWideThreads, 1) k_bounds_wide(JobDev *const *jobs) {
     const JobDev &J = *jobs[blockIdx.y];
     if (J.flags[0] != 0) return;
     extern __shared__ float4 smem4[];
     unsigned char *dyn = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem4) + 1023) & ~uintptr_t(1023));
-    __shared__ uint64_t bars[4];
+    __shared__ uint64_t bars[kWideBars];
     __shared__ uint32_t slot;
-    __shared__ float red[2 * kTcM];
-    WideWork W{};
-    wide_setup(W, dyn, bars, &slot, J.p);
     const int ntiles = tc_num_tiles(J.n_l, J.n_m);
     const int mine = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    for (int pass = 0; pass < 2; ++pass) {
-        float *dst = pass == 0 ? J.dirty : J.h;
-        wide_adjoint<MODE == 2>(J, W, J.Bimg + (size_t)pass * wide_B_bytes(J.p), J.Bscale[pass], blockIdx.x,
-                                gridDim.x, mine, red, [&](int i, float v) { dst[i] = v; });
-    }
-    if (W.timeouts && threadIdx.x == 0) J.flags[2] = IMG_ETIMEOUT;
-    wide_teardown(W, J.p);
+    float *dirty = J.dirty, *h = J.h;
+    const int to = wide_adjoint<MODE == 2>(J, dyn, bars, &slot, J.Bimg, J.Bimg + wide_B_bytes(J.p), J.Bscale, 2,
+                                           blockIdx.x, gridDim.x, mine,
+                                           [&](int s, int i, float v) { (s == 0 ? dirty : h)[i] = v; });
+    if (to && threadIdx.x == 0) J.flags[2] = IMG_ETIMEOUT;
 }
 
+// B image of one operator U for k_psi_adj_wide; grid (chunks, row blocks).
 template <int MODE>
 __global__ void k_emb_one(const JobDev *Jp, const float2 *U) {
-    emb_B_cta<MODE == 2>(U, Jp->p, Jp->Bimg, Jp->Bscale);
+    emb_B_chunk<MODE == 2>(U, Jp->p, Jp->Bimg, Jp->Bscale, blockIdx.x, blockIdx.y);
 }
 
 // Wide tensor-core Psi^H vect(U) over all pixels of one job.
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, 1) k_psi_adj_wide(const JobDev *Jp, double *out) {
+__global__ void __launch_bounds__(kWideThreads, 1) k_psi_adj_wide(const JobDev *Jp, double *out) {
     const JobDev &J = *Jp;
     extern __shared__ float4 smem4[];
     unsigned char *dyn = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem4) + 1023) & ~uintptr_t(1023));
-    __shared__ uint64_t bars[4];
+    __shared__ uint64_t bars[kWideBars];
     __shared__ uint32_t slot;
-    __shared__ float red[2 * kTcM];
-    WideWork W{};
-    wide_setup(W, dyn, bars, &slot, J.p);
     const int ntiles = tc_num_tiles(J.n_l, J.n_m);
     const int mine = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    wide_adjoint<MODE == 2>(J, W, J.Bimg, J.Bscale[0], blockIdx.x, gridDim.x, mine, red,
-                            [&](int i, float v) { out[i] = v; });
-    wide_teardown(W, J.p);
+    wide_adjoint<MODE == 2>(J, dyn, bars, &slot, J.Bimg, J.Bimg, J.Bscale, 1, blockIdx.x, gridDim.x, mine,
+                            [&](int, int i, float v) { out[i] = v; });
 }
 
 // Bounds, preconditioner and thresholds (one CTA per job):
@@ -1123,7 +1121,7 @@ static cudaError_t launch_bounds_tc_t(JobDev *const *jobs, int n, int max_tiles,
 
 template <int MODE>
 static cudaError_t launch_bounds_wide_t(JobDev *const *jobs, int n, int max_tiles, int max_p, cudaStream_t st) {
-    k_emb_bounds<MODE><<<dim3(n, 2), kThreads, 0, st>>>(jobs);
+    k_emb_bounds<MODE><<<dim3(n, 2, wide_nk(max_p) * (2 * kWideMaxP / kEmbRows)), kThreads, 0, st>>>(jobs);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t sm = wide_smem_bytes(max_p);
@@ -1131,7 +1129,7 @@ static cudaError_t launch_bounds_wide_t(JobDev *const *jobs, int n, int max_tile
     if (e != cudaSuccess) return e;
     int per_job = (num_sms() + n - 1) / n;
     per_job = max(1, min(per_job, max_tiles));
-    k_bounds_wide<MODE><<<dim3(per_job, n), kThreads, sm, st>>>(jobs);
+    k_bounds_wide<MODE><<<dim3(per_job, n), kWideThreads, sm, st>>>(jobs);
     return cudaGetLastError();
 }
 
@@ -1235,14 +1233,14 @@ static cudaError_t launch_psi_adj_tc_t(const JobDev *job_dev, const float2 *U, d
 template <int MODE>
 static cudaError_t launch_psi_adj_wide_t(const JobDev *job_dev, const float2 *U, double *out, int Q, int p,
                                          cudaStream_t st) {
-    k_emb_one<MODE><<<1, kThreads, 0, st>>>(job_dev, U);
+    k_emb_one<MODE><<<dim3(wide_nk(p), 2 * wide_kp(p) / kEmbRows), kThreads, 0, st>>>(job_dev, U);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t sm = wide_smem_bytes(p);
     e = ensure_smem((const void *)k_psi_adj_wide<MODE>, sm);
     if (e != cudaSuccess) return e;
     const int ntiles = (Q + kTcM - 1) / kTcM + 64;
-    k_psi_adj_wide<MODE><<<min(ntiles, num_sms()), kThreads, sm, st>>>(job_dev, out);
+    k_psi_adj_wide<MODE><<<min(ntiles, num_sms()), kWideThreads, sm, st>>>(job_dev, out);
     return cudaGetLastError();
 }
 

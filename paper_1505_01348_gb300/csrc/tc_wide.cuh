@@ -1,43 +1,70 @@
-// Tensor-core adjoint Psi^H for wide arrays, 64 < p <= 256 (Kp = p rounded
-// up to 32, N = K = 2Kp <= 512): out_i = x_i^T B x_i as in tc_ops.cuh, but
-// the 2Kp x 2Kp operand B no longer fits in shared memory.  k_emb_B writes B
-// once per operator to global memory as K-chunks of 64 columns, each the
-// exact shared-memory image of a swizzled K-major tile (hi part then lo part),
-// and the operator kernel streams chunk c into shared memory with a bulk TMA
-// copy (cp.async.bulk, completion counted in bytes on an mbarrier) while the
-// CTA generates the matching 64-column chunk of the steering tile; chunks are
-// double-buffered so copies and generation overlap the MMAs of the previous
-// chunk.  The FP32 accumulator (2Kp columns of tensor memory) sums the chunks;
-// the epilogue rebuilds x_i from the steering tables.
+// Tensor-core adjoint Psi^H for wide arrays, 64 < p <= 256: out_i =
+// x_i^T B x_i with x_i = [Re a_i; Im a_i] and B the real embedding of U
+// (Sec. V-B), as in tc_ops.cuh, but the 2Kp x 2Kp operand (Kp = p rounded up
+// to 32, N = 2Kp) no longer fits in shared memory.
+//
+// * emb_B_chunk writes B once per operator to global memory (L2-resident, at
+//   most 2 MB) as K-chunks of 64 columns; each chunk is one or two "units",
+//   each the exact shared-memory image (hi part, then lo part) of a swizzled
+//   K-major tile of at most 256 rows, so a unit moves with one bulk copy
+//   (cp.async.bulk, completion counted in bytes on an mbarrier).
+// * The operator is warp-specialised, with mbarrier hand-offs only:
+//     warps 0-3  epilogue: tensor memory -> x_i^T (B x_i), one pixel per
+//                thread, table rows staged per warp by asynchronous copies;
+//     warps 4-7  steering producers: 64-column chunks of the 128-pixel tile
+//                (FP32 products of the separable tables, split hi + lo);
+//     warp 8     copies of B units and the MMAs (lane 0 issues).
+//   Two X stages, two B stages (64 KB each) and two accumulator regions of
+//   256 tensor-memory columns: for Kp <= 128 consecutive tiles alternate
+//   regions, so the epilogue of one tile overlaps the MMAs of the next; for
+//   Kp > 128 each tile spans both regions (B rows split in two units) and a
+//   region is handed back as soon as the epilogue has read it.
 #pragma once
 #include "tc_ops.cuh"
 
 namespace img {
 
 constexpr int kWideMaxP = 256;
-constexpr int kChunkK = 64;                 // K columns per streamed chunk
+constexpr int kChunkK = 64;                 // K columns per chunk (one 128-byte swizzle atom)
+constexpr int kWideThreads = 288;           // 9 warps
+constexpr size_t kWideXStage = 2 * kTcM * 128;       // hi + lo, 32 KB
+constexpr size_t kWideBStage = 64 * 1024;
 
 __host__ __device__ inline int wide_kp(int p) { return (p + 31) / 32 * 32; }
-// Bytes of one global B chunk (hi + lo): N rows x 128 bytes, twice.
-__host__ __device__ inline size_t wide_chunk_bytes(int p) { return (size_t)2 * (2 * wide_kp(p)) * 128; }
-// Bytes of the whole chunked B image.
-__host__ __device__ inline size_t wide_B_bytes(int p) {
-    return wide_chunk_bytes(p) * (2 * wide_kp(p) / kChunkK);
-}
-// Shared memory: two X chunks (128 rows x 128 B, hi + lo) and one or two B
-// chunks (two when N <= 256).
-__host__ __device__ inline int wide_nb(int p) { return 2 * wide_kp(p) <= 256 ? 2 : 1; }
-__host__ __device__ inline size_t wide_smem_bytes(int p) {
-    return (size_t)2 * 2 * kTcM * 128 + (size_t)wide_nb(p) * wide_chunk_bytes(p) + 1024;
-}
-__host__ __device__ inline uint32_t wide_tmem_cols(int p) {
-    const int n = 2 * wide_kp(p);
-    uint32_t c = 32;
-    while ((int)c < n) c <<= 1;
-    return c;
+// B units per chunk: two when N = 2Kp > 256 (one MMA takes N <= 256).
+__host__ __device__ inline int wide_units(int p) { return 2 * wide_kp(p) > 256 ? 2 : 1; }
+__host__ __device__ inline int wide_unit_rows(int p) { return wide_units(p) == 2 ? wide_kp(p) : 2 * wide_kp(p); }
+__host__ __device__ inline size_t wide_unit_bytes(int p) { return (size_t)2 * wide_unit_rows(p) * 128; }
+__host__ __device__ inline size_t wide_chunk_bytes(int p) { return (size_t)2 * 2 * wide_kp(p) * 128; }
+__host__ __device__ inline int wide_nk(int p) { return 2 * wide_kp(p) / kChunkK; }
+__host__ __device__ inline size_t wide_B_bytes(int p) { return wide_chunk_bytes(p) * wide_nk(p); }
+// Epilogue staging per warp: 3 buffers x 12 table rows x 16 k (row stride
+// 18 float2, so 16-byte reads of the 8 E_l rows hit distinct banks).
+constexpr int kEpiRow = 18;
+constexpr size_t kEpiStage = (size_t)3 * 12 * kEpiRow * 8;
+__host__ __device__ inline size_t wide_smem_bytes(int) {
+    return 2 * kWideXStage + 2 * kWideBStage + 4 * kEpiStage + 1024;
 }
 
-// ---------------------------------------------------------------- TMA bulk copy
+// Row n of B (the N index, i.e. column n of the accumulator) holds the
+// (part, k) of x it multiplies in the epilogue.  One unit: [Re 0..Kp-1,
+// Im 0..Kp-1].  Two units: unit g holds k in [g*h, (g+1)*h), h = Kp/2, as
+// [Re ..., Im ...], so each accumulator region covers both parts of its k.
+__device__ __forceinline__ void wide_row(int n, int Kp, int nu, int &part, int &k) {
+    if (nu == 1) {
+        part = n >= Kp;
+        k = n - part * Kp;
+    } else {
+        const int h = Kp >> 1, g = n / Kp, r = n - g * Kp;
+        part = r >= h;
+        k = g * h + r - part * h;
+    }
+}
+
+// ---------------------------------------------------------------- barriers, bulk copy
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
@@ -51,248 +78,423 @@ __device__ __forceinline__ void tma_bulk_g2s(void *dst, const void *src, uint32_
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
+// Two 16-column tensor-memory loads, one wait.
+__device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float *a, float *b) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+        "[%32];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, "
+        "[%33];\n"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+          "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+          "=r"(r[30]), "=r"(r[31])
+        : "r"(ta), "r"(tb)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        a[i] = __uint_as_float(r[i]);
+        b[i] = __uint_as_float(r[16 + i]);
+    }
+}
+
+// Two values -> hi and lo 16-bit pairs (packed conversions, round to nearest).
+template <bool BF16>
+__device__ __forceinline__ void split2(float v0, float v1, uint32_t &hi, uint32_t &lo) {
+    if (BF16) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+        hi = *reinterpret_cast<const uint32_t *>(&h);
+        lo = *reinterpret_cast<const uint32_t *>(&l);
+    } else {
+        const __half2 h = __floats2half2_rn(v0, v1);
+        const float2 hf = __half22float2(h);
+        const __half2 l = __floats2half2_rn(v0 - hf.x, v1 - hf.y);
+        hi = *reinterpret_cast<const uint32_t *>(&h);
+        lo = *reinterpret_cast<const uint32_t *>(&l);
+    }
+}
+
+// 8-byte asynchronous global -> shared copy (zero-filled when !valid; src
+// must still be a readable address).
+__device__ __forceinline__ void cp_async8(void *dst, const void *src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src),
+                 "r"(valid ? 8 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;" ::: "memory"); }
 
 // ---------------------------------------------------------------- B image
-// One CTA writes the chunked image of B = emb(U) (rows [Re V, -Im V],
-// [Im V, Re V] with V = U^H, the same quadratic form) scaled by a power of
-// two to unit range; *scale receives that factor.
-template <bool BF16>
-__device__ void emb_B_cta(const float2 *U, int p, unsigned char *img, float *scale) {
-    const int Kp = wide_kp(p), nc8 = Kp / 8;
-    __shared__ float sred[kThreads / 32];
+// Power-of-two scale that brings max |U| to (1/2, 1], computed by every CTA
+// (p^2 <= 65536 complex entries, read as float4 pairs, 8 loads in flight).
+__device__ inline float emb_scale(const float2 *U, int p) {
+    __shared__ float sred[32];
+    const int n2 = p * p, nv = n2 >> 1;
     float mx = 0.f;
-    for (int e = threadIdx.x; e < p * p; e += blockDim.x)
-        mx = fmaxf(mx, fmaxf(fabsf(U[e].x), fabsf(U[e].y)));
+    if ((reinterpret_cast<uintptr_t>(U) & 15) == 0) {
+        const float4 *U4 = reinterpret_cast<const float4 *>(U);
+        int e = threadIdx.x;
+        for (; e + 7 * (int)blockDim.x < nv; e += 8 * blockDim.x) {
+            float4 v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = U4[e + q * blockDim.x];
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v[q].x), fabsf(v[q].y)), fmaxf(fabsf(v[q].z), fabsf(v[q].w))));
+        }
+        for (; e < nv; e += blockDim.x) {
+            const float4 v = U4[e];
+            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+        }
+        if ((n2 & 1) && threadIdx.x == 0) mx = fmaxf(mx, fmaxf(fabsf(U[n2 - 1].x), fabsf(U[n2 - 1].y)));
+    } else {
+        for (int e = threadIdx.x; e < n2; e += blockDim.x) mx = fmaxf(mx, fmaxf(fabsf(U[e].x), fabsf(U[e].y)));
+    }
     for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = mx;
     __syncthreads();
     mx = 0.f;
-    for (int w = 0; w < kThreads / 32; ++w) mx = fmaxf(mx, sred[w]);
-    const float sc = mx > 0.f ? exp2f(-ceilf(log2f(mx))) : 1.f;
-    if (threadIdx.x == 0) *scale = sc;
-    const size_t cb = wide_chunk_bytes(p), half = cb / 2;
-    for (int it = threadIdx.x; it < Kp * nc8; it += blockDim.x) {
-        const int n = it / nc8, c8 = it - n * nc8;
-        const int k0 = c8 * 8;
-        float re[8], im[8], nim[8];
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) mx = fmaxf(mx, sred[w]);
+    __syncthreads();
+    return mx > 0.f ? exp2f(-ceilf(log2f(mx))) : 1.f;
+}
+
+// Rows per CTA of the B image kernels (grid: chunks x N / kEmbRows).
+constexpr int kEmbRows = 64;
+
+// Rows [rb * kEmbRows, +kEmbRows) of chunk kc of the B image of U
+// (column-major p x p): B = emb(V), V = U^H, whose quadratic form equals
+// that of emb(U).  With u = U[k_row * p + k_col] (= conj V(k_row, k_col)):
+// blocks (Re, Re) and (Im, Im) hold u.x, (Re, Im) holds u.y, (Im, Re) holds
+// -u.y.  The CTA of chunk 0, row block 0 stores the scale.
+template <bool BF16>
+__device__ void emb_B_chunk(const float2 *U, int p, unsigned char *img, float *scale, int kc, int rb) {
+    const int Kp = wide_kp(p), nc8 = Kp / 8, nu = wide_units(p), rows_u = wide_unit_rows(p);
+    const float sc = emb_scale(U, p);
+    if (kc == 0 && rb == 0 && threadIdx.x == 0) *scale = sc;
+    unsigned char *chunk = img + (size_t)kc * wide_chunk_bytes(p);
+    const size_t ub = wide_unit_bytes(p);
+    for (int it = threadIdx.x; it < kEmbRows * 8; it += blockDim.x) {
+        const int n = rb * kEmbRows + (it >> 3), cc = it & 7;
+        const int g = kc * 8 + cc;                    // global 8-column group
+        const int cpart = g >= nc8, k0 = (g - cpart * nc8) * 8;
+        int rpart, kr;
+        wide_row(n, Kp, nu, rpart, kr);
+        float v[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             float2 u = make_float2(0.f, 0.f);
-            if (n < p && k0 + e < p) u = U[(size_t)n * p + k0 + e];   // U(k, n) = conj(V(n, k))
-            re[e] = u.x * sc;
-            im[e] = -u.y * sc;
-            nim[e] = u.y * sc;
+            if (kr < p && k0 + e < p) u = U[(size_t)kr * p + k0 + e];
+            const float val = (rpart == cpart) ? u.x : (rpart == 0 ? u.y : -u.y);
+            v[e] = val * sc;
         }
-        // column chunk c (8 columns): K-chunk kc = c / 8, chunk cc = c % 8 in it
-        auto put = [&](int row, int c, const float *v) {
-            uint4 hi, lo;
-            split8<BF16>(v, hi, lo);
-            const int kc = c >> 3, cc = c & 7;
-            const size_t off = (size_t)kc * cb + (size_t)(row >> 3) * 1024 + (row & 7) * 128 +
-                               ((cc ^ (row & 7)) << 4);
-            *reinterpret_cast<uint4 *>(img + off) = hi;
-            *reinterpret_cast<uint4 *>(img + off + half) = lo;
-        };
-        put(n, c8, re);              // (re row, re col): Re V
-        put(Kp + n, nc8 + c8, re);   // (im row, im col): Re V
-        put(n, nc8 + c8, nim);       // (re row, im col): -Im V
-        put(Kp + n, c8, im);         // (im row, re col): Im V
+        uint4 hi, lo;
+        split8<BF16>(v, hi, lo);
+        const int un = n / rows_u, rr = n - un * rows_u;
+        const size_t off = (size_t)un * ub + (size_t)(rr >> 3) * 1024 + (rr & 7) * 128 + ((cc ^ (rr & 7)) << 4);
+        *reinterpret_cast<uint4 *>(chunk + off) = hi;
+        *reinterpret_cast<uint4 *>(chunk + off + (size_t)rows_u * 128) = lo;
     }
 }
 
 // ---------------------------------------------------------------- operator
-struct WideWork {
-    unsigned char *X[2];      // X chunk buffers (hi at +0, lo at +16 KB)
-    unsigned char *B[2];      // B chunk buffers (one or two)
-    uint64_t *barB;           // 2 barriers: a B chunk landed
-    uint64_t *barM;           // 2 barriers: the MMAs of a chunk completed
-    uint32_t phB[2], phM[2];
-    int issued[2], waited[2]; // MMA commits per barrier (all threads agree)
-    uint32_t tmem;
-    int Kp, nb, timeouts;
-};
+// Barrier slots in the caller's kWideBars-entry shared array.
+enum : int { kBFull = 0, kBEmpty = 2, kXFull = 4, kXEmpty = 6, kAFull = 8, kAEmpty = 10, kWideBars = 12 };
 
-__device__ inline void wide_setup(WideWork &W, unsigned char *base, uint64_t *bars, uint32_t *slot, int p) {
-    W.Kp = wide_kp(p);
-    W.nb = wide_nb(p);
-    W.X[0] = base;
-    W.X[1] = base + 2 * kTcM * 128;
-    W.B[0] = base + 4 * kTcM * 128;
-    W.B[1] = W.B[0] + wide_chunk_bytes(p);
-    W.barB = bars;
-    W.barM = bars + 2;
-    W.phB[0] = W.phB[1] = W.phM[0] = W.phM[1] = 0;
-    W.issued[0] = W.issued[1] = W.waited[0] = W.waited[1] = 0;
-    W.timeouts = 0;
-    if (threadIdx.x == 0)
-        for (int k = 0; k < 4; ++k) mbar_init(&bars[k], 1);
-    if (threadIdx.x < 32) tmem_alloc(slot, wide_tmem_cols(p));
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    W.tmem = *slot;
-}
-
-// Wait for the oldest outstanding MMA commit on barrier b, if any.
-__device__ __forceinline__ void wide_wait_mma(WideWork &W, int b) {
-    if (W.waited[b] < W.issued[b]) {
-        if (!mbar_wait(&W.barM[b], W.phM[b])) W.timeouts++;
-        W.phM[b] ^= 1u;
-        W.waited[b]++;
+// Wait for the next phase of barrier `slot`; its parity is bit `slot` of ph.
+// After one wait of this thread has timed out the pipeline is broken: later
+// waits poll once, so the kernel still ends in bounded time (and reports).
+__device__ __forceinline__ void wide_wait(uint64_t *bars, int slot, uint32_t &ph, int &timeouts) {
+    const uint32_t par = (ph >> slot) & 1u;
+    ph ^= 1u << slot;
+    if (timeouts) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_u32(&bars[slot])), "r"(par)
+            : "memory");
+        if (!done) timeouts++;
+        return;
     }
+    if (!mbar_wait(&bars[slot], par)) timeouts++;
 }
 
-__device__ inline void wide_teardown(WideWork &W, int p) {
-    wide_wait_mma(W, 0);
-    wide_wait_mma(W, 1);
-    tc_fence_before();
-    __syncthreads();
-    if (threadIdx.x < 32) tmem_dealloc(W.tmem, wide_tmem_cols(p));
-}
-
-// Chunk kc (columns kc*64 .. kc*64+63 of the 2Kp) of the steering tile t
-// into X buffer b.  Column col < Kp holds Re a_col, col >= Kp holds
-// Im a_(col-Kp); an 8-column group never straddles the boundary (Kp is a
-// multiple of 32), but a 64-column chunk may.
-template <bool BF16>
-__device__ inline void wide_gen_X(const JobDev &J, const WideWork &W, int b, int t, int kc, float sX) {
-    const int p = J.p, Kp = W.Kp, nl = J.n_l;
-    unsigned char *xh = W.X[b], *xl = W.X[b] + kTcM * 128;
-    const float2 *__restrict__ El = J.El;
-    const float2 *__restrict__ Em = J.Em;
-    for (int it = threadIdx.x; it < kTcM * 8; it += blockDim.x) {
-        const int r = it >> 3, c8 = it & 7;
-        const int i = tc_tile_pixel(t, r, nl, J.n_m);
-        const int col = kc * kChunkK + c8 * 8;
-        const bool re_part = col < Kp;
-        const int k0 = re_part ? col : col - Kp;
-        float v[8];
-        if (i >= 0) {
-            const int mm = i / nl, ll = i - mm * nl;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int k = k0 + q;
-                float2 a = make_float2(0.f, 0.f);
-                if (k < p) a = cmul(__ldg(El + (size_t)ll * p + k), __ldg(Em + (size_t)mm * p + k));
-                v[q] = (re_part ? a.x : a.y) * sX;
-            }
-        } else {
-#pragma unroll
-            for (int q = 0; q < 8; ++q) v[q] = 0.f;
-        }
-        uint4 hi, lo;
-        split8<BF16>(v, hi, lo);
-        const uint32_t off = (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c8 ^ (r & 7)) << 4));
-        *reinterpret_cast<uint4 *>(xh + off) = hi;
-        *reinterpret_cast<uint4 *>(xl + off) = lo;
-    }
-}
-
-// MMAs of one K-chunk: X buffer bx (128 rows) against B buffer bb (N rows),
-// 4 K-steps x 3 split products; N above 256 takes a second MMA per step.
-__device__ inline void wide_issue(const WideWork &W, int bx, int bb, bool first, int BF) {
-    const int N = 2 * W.Kp;
-    const int n_lo = N <= 256 ? N : 256, n_hi = N - n_lo;
-    const uint32_t id_lo = idesc_f16(n_lo, BF), id_hi = idesc_f16(n_hi > 0 ? n_hi : 16, BF);
-    tc_fence_after();
-    const uint32_t xh = smem_u32(W.X[bx]), xl = xh + kTcM * 128;
-    const uint32_t bh = smem_u32(W.B[bb]), bl = bh + N * 128;
-    for (int s = 0; s < kChunkK / 16; ++s) {
-        const uint32_t o = s * 32;
-        const uint32_t acc = (first && s == 0) ? 0u : 1u;
-        mma_f16(W.tmem, sw128_desc(xh + o), sw128_desc(bh + o), id_lo, acc);
-        mma_f16(W.tmem, sw128_desc(xh + o), sw128_desc(bl + o), id_lo, 1u);
-        mma_f16(W.tmem, sw128_desc(xl + o), sw128_desc(bh + o), id_lo, 1u);
-        if (n_hi > 0) {
-            const uint32_t bo = (uint32_t)n_lo * 128, d = W.tmem + (uint32_t)n_lo;
-            mma_f16(d, sw128_desc(xh + o), sw128_desc(bh + bo + o), id_hi, acc);
-            mma_f16(d, sw128_desc(xh + o), sw128_desc(bl + bo + o), id_hi, 1u);
-            mma_f16(d, sw128_desc(xl + o), sw128_desc(bh + bo + o), id_hi, 1u);
-        }
-    }
-}
-
-// out_i = Re(a_i^H U a_i) over the 2-D tiles t0, t0 + dt, ... (ntiles), with
-// the chunked B image Bimg (scale sB) streamed by bulk copies.  epi(i, v).
+// out = Re(a_i^H U_s a_i) for npass <= 2 operators s (B images B0, B1,
+// scales sB[s]) over the 2-D tiles t0, t0 + dt, ... (ntiles of them);
+// epi(s, i, v) receives each pixel's value.  Needs kWideThreads threads,
+// 1024-aligned dynamic shared memory `dyn` of wide_smem_bytes(p) - 1024
+// bytes and kWideBars mbarriers.  Returns the number of waits that timed out.
 template <bool BF16, class Epi>
-__device__ void wide_adjoint(const JobDev &J, WideWork &W, const unsigned char *Bimg, float sB, int t0, int dt,
-                             int ntiles, float *red, Epi epi) {
-    const int p = J.p, Kp = W.Kp, N = 2 * Kp, nk = N / kChunkK;
-    const float sX = steer_scale(p);
-    const float inv = 1.f / (sX * sB);
-    const uint32_t cbytes = (uint32_t)wide_chunk_bytes(p);
-    const int total = ntiles * nk;
-    if (total == 0) return;
+__device__ int wide_adjoint(const JobDev &J, unsigned char *dyn, uint64_t *bars, uint32_t *slot,
+                            const unsigned char *B0, const unsigned char *B1, const float *sB, int npass,
+                            int t0, int dt, int ntiles, Epi epi) {
+    const int p = J.p, Kp = wide_kp(p), nk = wide_nk(p), nu = wide_units(p), rows_u = wide_unit_rows(p);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char *Xs = dyn, *Bs = dyn + 2 * kWideXStage;
+    __shared__ int s_timeouts;
     if (threadIdx.x == 0) {
-        mbar_expect_tx(&W.barB[0], cbytes);
-        tma_bulk_g2s(W.B[0], Bimg, cbytes, &W.barB[0]);
+        s_timeouts = 0;
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&bars[kBFull + q], 1);
+            mbar_init(&bars[kBEmpty + q], 1);
+            mbar_init(&bars[kXFull + q], 4);
+            mbar_init(&bars[kXEmpty + q], 1);
+            mbar_init(&bars[kAFull + q], 1);
+            mbar_init(&bars[kAEmpty + q], 4);
+        }
     }
-    for (int c = 0; c < total; ++c) {
-        const int tt = c / nk, kc = c - tt * nk;
-        const int t = t0 + tt * dt;
-        const int bx = c & 1, bb = W.nb == 2 ? (c & 1) : 0;
-        wide_wait_mma(W, bx);                       // X[bx] free: MMAs of chunk c-2 done
-        wide_gen_X<BF16>(J, W, bx, t, kc, sX);
-        fence_async_smem();
-        if (!mbar_wait(&W.barB[bb], W.phB[bb])) W.timeouts++;   // B chunk c landed
-        W.phB[bb] ^= 1u;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            wide_issue(W, bx, bb, kc == 0, BF16 ? 1 : 0);
-            mma_commit(&W.barM[bx]);
-        }
-        W.issued[bx]++;
-        if (c + 1 < total) {
-            // the next B chunk goes to a buffer no pending MMA reads
-            const int nbb = W.nb == 2 ? ((c + 1) & 1) : 0;
-            wide_wait_mma(W, W.nb == 2 ? ((c + 1) & 1) : bx);
-            if (threadIdx.x == 0) {
-                const int nkc = (c + 1) % nk;
-                mbar_expect_tx(&W.barB[nbb], cbytes);
-                tma_bulk_g2s(W.B[nbb], Bimg + (size_t)nkc * cbytes, cbytes, &W.barB[nbb]);
+    if (warp == 0) tmem_alloc(slot, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *slot;
+    const float sX = steer_scale(p);
+    const int tiles = npass * ntiles;             // tile uses, pass-major
+    const int total = tiles * nk;                 // X chunks
+    const int nl = J.n_l, nm = J.n_m, tl = (nl + kTileL - 1) / kTileL;
+    int timeouts = 0;
+
+    if (warp == 8) {
+        // ---------------- copies and MMAs.  The whole warp walks the unit
+        // sequence and waits (warp-uniform control flow); lane 0 issues.
+        // Unit u = (chunk c, part pp) uses B stage u & 1; the copy of unit
+        // u + 1 is issued once the MMAs of unit u - 1 released its stage.
+        if (total > 0) {
+            const bool leader = lane == 0;
+            const uint32_t ub = (uint32_t)wide_unit_bytes(p);
+            const size_t cb = wide_chunk_bytes(p);
+            const uint32_t idesc = idesc_f16(rows_u, BF16 ? 1 : 0);
+            const int units = total * nu;
+            uint32_t ph = 0;
+            const int first_reuse = nu == 2 ? 1 : 2;   // first use of a region needs no hand-back
+            auto src = [&](int u) {
+                const int c = u / nu, pp = u - c * nu, T = c / nk, kc = c - T * nk;
+                return (T < ntiles ? B0 : B1) + (size_t)kc * cb + (size_t)pp * ub;
+            };
+            if (leader) {
+                mbar_expect_tx(&bars[kBFull], ub);
+                tma_bulk_g2s(Bs, src(0), ub, &bars[kBFull]);
             }
-        }
-        if (kc == nk - 1) {
-            // tile complete: its last MMAs, then the epilogue from tensor memory
-            wide_wait_mma(W, bx);
-            tc_fence_after();
-            __syncthreads();
-            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-            const int half = warp >> 2, r = 32 * (warp & 3) + lane;
-            const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-            const int i = tc_tile_pixel(t, r, J.n_l, J.n_m);
-            int mm = 0, ll = 0;
-            if (i >= 0) {
-                mm = i / J.n_l;
-                ll = i - mm * J.n_l;
-            }
-            float acc = 0.f;
-            for (int c0 = 0; c0 < Kp; c0 += 16) {
-                float d[16];
-                tmem_ld16(W.tmem + lane_base + (uint32_t)(half * Kp + c0), d);
-                if (i >= 0) {
+            for (int u = 0; u < units; ++u) {
+                const int c = u / nu, pp = u - c * nu, T = c / nk, kc = c - T * nk, s = u & 1;
+                if (pp == 0) wide_wait(bars, kXFull + (c & 1), ph, timeouts);
+                const int g = nu == 2 ? pp : (T & 1);
+                if (kc == 0 && T >= first_reuse) wide_wait(bars, kAEmpty + g, ph, timeouts);
+                wide_wait(bars, kBFull + s, ph, timeouts);
+                tc_fence_after();
+                if (leader) {
+                    const uint32_t xh = smem_u32(Xs + (c & 1) * kWideXStage), xl = xh + kTcM * 128;
+                    const uint32_t bh = smem_u32(Bs + s * kWideBStage), bl = bh + (uint32_t)rows_u * 128;
+                    const uint32_t d = tmem + (uint32_t)(g * 256);
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        const int k = c0 + q;
-                        if (k < p) {
-                            const float2 a = cmul(__ldg(J.El + (size_t)ll * p + k), __ldg(J.Em + (size_t)mm * p + k));
-                            acc = fmaf(half ? a.y : a.x, d[q], acc);
-                        }
+                    for (int st = 0; st < kChunkK / 16; ++st) {
+                        const uint32_t o = st * 32;
+                        mma_f16(d, sw128_desc(xh + o), sw128_desc(bh + o), idesc, (kc > 0 || st > 0) ? 1u : 0u);
+                        mma_f16(d, sw128_desc(xh + o), sw128_desc(bl + o), idesc, 1u);
+                        mma_f16(d, sw128_desc(xl + o), sw128_desc(bh + o), idesc, 1u);
+                    }
+                    mma_commit(&bars[kBEmpty + s]);
+                    if (pp == nu - 1) mma_commit(&bars[kXEmpty + (c & 1)]);
+                    if (kc == nk - 1) mma_commit(&bars[kAFull + g]);
+                }
+                __syncwarp();
+                if (u + 1 < units) {
+                    // stage s^1 was last read by the MMAs of unit u - 1
+                    const int s1 = s ^ 1;
+                    if (u >= 1) wide_wait(bars, kBEmpty + s1, ph, timeouts);
+                    if (leader) {
+                        mbar_expect_tx(&bars[kBFull + s1], ub);
+                        tma_bulk_g2s(Bs + s1 * kWideBStage, src(u + 1), ub, &bars[kBFull + s1]);
                     }
                 }
             }
-            red[half * kTcM + r] = acc;
-            tc_fence_before();
-            __syncthreads();
-            if (threadIdx.x < kTcM) {
-                const int ii = tc_tile_pixel(t, threadIdx.x, J.n_l, J.n_m);
-                if (ii >= 0) epi(ii, (red[threadIdx.x] + red[kTcM + threadIdx.x]) * inv);
+        }
+    } else if (warp >= 4) {
+        // ---------------- steering producers: chunk c of tile use T into X stage c & 1.
+        // Warp w fills rows 32w + 8b + a (l offset a = 0..7, m offset 4w + b),
+        // lane j columns 2j, 2j+1 of the chunk; all 12 table loads of a chunk
+        // are issued before the wait for the stage.
+        const int w = warp - 4;
+        const bool vec = (p & 1) == 0;
+        const float2 *__restrict__ El = J.El;
+        const float2 *__restrict__ Em = J.Em;
+        // byte offset of (row 32w + a, this lane's column pair); row 32w + 8b + a adds b * 1024
+        uint32_t xo[8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+            xo[a] = (uint32_t)(4 * w * 1024 + a * 128 + (((lane >> 2) ^ a) << 4) + (lane & 3) * 4);
+        uint32_t ph = 0;
+        // the 12 table loads of chunk c + 1 are in flight while chunk c is written
+        float2 e[8][2], f[4][2];
+        auto load = [&](int c) {
+            const int T = c / nk, kc = c - T * nk;
+            const int t = t0 + (T % ntiles) * dt;
+            const int bm = t / tl, bl = t - bm * tl;
+            const int il0 = bl * kTileL, im0 = bm * kTileM + 4 * w;
+            const int col = kc * kChunkK + 2 * lane;
+            const int k = col >= Kp ? col - Kp : col;
+#pragma unroll
+            for (int a = 0; a < 8; ++a) {
+                const int il = il0 + a;
+                e[a][0] = e[a][1] = make_float2(0.f, 0.f);
+                if (il < nl && k < p) {
+                    const float2 *src = El + (size_t)il * p + k;
+                    if (vec) {
+                        const float4 v = __ldg(reinterpret_cast<const float4 *>(src));
+                        e[a][0] = make_float2(v.x, v.y);
+                        e[a][1] = make_float2(v.z, v.w);
+                    } else {
+                        e[a][0] = __ldg(src);
+                        if (k + 1 < p) e[a][1] = __ldg(src + 1);
+                    }
+                }
             }
-            __syncthreads();
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int im = im0 + b;
+                f[b][0] = f[b][1] = make_float2(0.f, 0.f);
+                if (im < nm && k < p) {
+                    const float2 *src = Em + (size_t)im * p + k;
+                    if (vec) {
+                        const float4 v = __ldg(reinterpret_cast<const float4 *>(src));
+                        f[b][0] = make_float2(v.x, v.y);
+                        f[b][1] = make_float2(v.z, v.w);
+                    } else {
+                        f[b][0] = __ldg(src);
+                        if (k + 1 < p) f[b][1] = __ldg(src + 1);
+                    }
+                }
+            }
+        };
+        if (total > 0) load(0);
+        for (int c = 0; c < total; ++c) {
+            const int kc = c % nk, s = c & 1;
+            const int part = kc * kChunkK + 2 * lane >= Kp;
+            float2 ec[8][2], fc[4][2];
+#pragma unroll
+            for (int a = 0; a < 8; ++a) {
+                ec[a][0] = e[a][0];
+                ec[a][1] = e[a][1];
+            }
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                fc[b][0] = f[b][0];
+                fc[b][1] = f[b][1];
+            }
+            if (c + 1 < total) load(c + 1);
+            // v = Re(e f) = e.x (f.x) + e.y (-f.y), or Im(e f) = e.x (f.y) + e.y (f.x):
+            // fold the part and the scale into f once per chunk
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const float2 v = fc[b][q];
+                    fc[b][q] = part ? make_float2(v.y * sX, v.x * sX) : make_float2(v.x * sX, -v.y * sX);
+                }
+            if (c >= 2) wide_wait(bars, kXEmpty + s, ph, timeouts);
+            unsigned char *xh = Xs + s * kWideXStage, *xl = xh + kTcM * 128;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+#pragma unroll
+                for (int a = 0; a < 8; ++a) {
+                    const float v0 = fmaf(ec[a][0].x, fc[b][0].x, ec[a][0].y * fc[b][0].y);
+                    const float v1 = fmaf(ec[a][1].x, fc[b][1].x, ec[a][1].y * fc[b][1].y);
+                    uint32_t hi, lo;
+                    split2<BF16>(v0, v1, hi, lo);
+                    const uint32_t off = xo[a] + b * 1024;
+                    *reinterpret_cast<uint32_t *>(xh + off) = hi;
+                    *reinterpret_cast<uint32_t *>(xl + off) = lo;
+                }
+            }
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars[kXFull + s]);
+        }
+    } else {
+        // ---------------- epilogue: one pixel row per thread.  Each warp
+        // stages, 16 k at a time, the 8 E_l rows and its 4 E_m rows of the
+        // tile in shared memory (asynchronous copies, three buffers, two
+        // groups ahead), then reads the accumulator 2 x 16 columns at a time.
+        const int r = 32 * warp + lane;
+        const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+        const int wcols = nu == 2 ? Kp / 2 : Kp, ng = Kp / 16;
+        const float2 *__restrict__ El = J.El;
+        const float2 *__restrict__ Em = J.Em;
+        float2 *S = reinterpret_cast<float2 *>(Bs + 2 * kWideBStage + warp * kEpiStage);
+        uint32_t ph = 0;
+        for (int T = 0; T < tiles; ++T) {
+            const int pass = T / ntiles, t = t0 + (T - pass * ntiles) * dt;
+            const int bm = t / tl, bl = t - bm * tl;
+            const int il0 = bl * kTileL, im0 = bm * kTileM + 4 * warp;
+            // group gi: rows 0-7 E_l(il0 + row), rows 8-11 E_m(im0 + row - 8), k = 16 gi ..
+            auto issue = [&](int gi) {
+                if (gi < ng) {
+                    float2 *dst = S + (gi % 3) * 12 * kEpiRow;
+#pragma unroll
+                    for (int q0 = 0; q0 < 12 * 16; q0 += 32) {
+                        const int q = q0 + lane, row = q >> 4, kk = q & 15, k = gi * 16 + kk;
+                        const bool isl = row < kTileL;
+                        const int gr = isl ? il0 + row : im0 + row - kTileL;
+                        const bool ok = (isl ? gr < nl : gr < nm) && k < p;
+                        const float2 *src = ok ? (isl ? El : Em) + (size_t)gr * p + k : El;
+                        cp_async8(dst + row * kEpiRow + kk, src, ok);
+                    }
+                }
+                cp_async_commit();
+            };
+            issue(0);
+            issue(1);
+            const int i = tc_tile_pixel(t, r, nl, nm);
+            float acc = 0.f;
+            int grp = 0;
+            for (int pp = 0; pp < nu; ++pp) {
+                const int g = nu == 2 ? pp : (T & 1);
+                wide_wait(bars, kAFull + g, ph, timeouts);
+                tc_fence_after();
+                const uint32_t base = tmem + lane_base + (uint32_t)(g * 256);
+                for (int kk = 0; kk < wcols; kk += 16, ++grp) {
+                    issue(grp + 2);
+                    cp_async_wait2();
+                    __syncwarp();
+                    const float2 *sb = S + (grp % 3) * 12 * kEpiRow;
+                    const float4 *se = reinterpret_cast<const float4 *>(sb + (lane & 7) * kEpiRow);
+                    const float4 *sf = reinterpret_cast<const float4 *>(sb + (kTileL + (lane >> 3)) * kEpiRow);
+                    float ar[16], ai[16];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float4 ev = se[j], fv = sf[j];
+                        const float2 a0 = cmul(make_float2(ev.x, ev.y), make_float2(fv.x, fv.y));
+                        const float2 a1 = cmul(make_float2(ev.z, ev.w), make_float2(fv.z, fv.w));
+                        ar[2 * j] = a0.x;
+                        ai[2 * j] = a0.y;
+                        ar[2 * j + 1] = a1.x;
+                        ai[2 * j + 1] = a1.y;
+                    }
+                    float dr[16], di[16];
+                    tmem_ld16x2(base + kk, base + wcols + kk, dr, di);
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) acc = fmaf(ar[q], dr[q], fmaf(ai[q], di[q], acc));
+                    __syncwarp();
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bars[kAEmpty + g]);
+            }
+            if (i >= 0) epi(pass, i, acc / (sX * sB[pass]));
         }
     }
-    wide_wait_mma(W, 0);
-    wide_wait_mma(W, 1);
+    if (timeouts) atomicAdd(&s_timeouts, timeouts);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 512);
+    return s_timeouts;
 }
 
 }  // namespace img
