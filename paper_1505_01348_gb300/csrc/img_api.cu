@@ -109,6 +109,7 @@ size_t carve(img_ctx *c, char *base) {
     J.ev_count = cv.take<int>(1);
     J.Bimg = (p > img::kMaxTcP && p <= img::kMaxWideP) ? cv.take<unsigned char>(2 * img::wide_B_bytes(p)) : nullptr;
     J.Bscale = cv.take<float>(2);
+    J.Bmax = (p > img::kMaxTcP && p <= img::kMaxWideP) ? cv.take<unsigned>(2) : nullptr;
     J.info = cv.take<DevInfo>(1);
     J.flags = cv.take<int>(4);
     c->dj = cv.take<JobDev>(1);
@@ -486,6 +487,21 @@ img_status img_psi(img_ctx *c, const double *x, double *Kout, int on_device) {
 img_status img_psi_adj(img_ctx *c, const double *U, double *out, int on_device) {
     if (!c || !U || !out) return IMG_EINVAL;
     const int Q = c->hj.Q, p = c->prm.p;
+    const int om = op_mode_of(c);
+    if (om != 0 && p > img::kMaxTcP) {
+        // streamed tensor-core operator: its operand image is built from the
+        // complex128 U directly (the caller's device buffer, or a staged copy)
+        const double2 *Ud = reinterpret_cast<const double2 *>(U);
+        if (!on_device) {
+            CK(cudaMemcpyAsync(c->Z, U, (size_t)p * p * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+            Ud = c->Z;
+        }
+        CK(img::launch_psi_adj_wide(c->dj, c->hj.Bmax, Ud, true, on_device ? out : c->outd, Q, p, om,
+                                    c->stream));
+        if (on_device == 2) return IMG_OK;
+        if (on_device) return sync(c);
+        return copy_out_double(c, c->outd, out, Q, 0);
+    }
     CK(cudaMemcpyAsync(c->Z, U, (size_t)p * p * sizeof(double2),
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     CK(img::launch_z2c(c->Z, c->U32, p * p, c->stream));

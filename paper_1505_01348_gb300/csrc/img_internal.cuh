@@ -76,6 +76,7 @@ struct JobDev {
     // operators (64 < p <= 256), and their scales
     unsigned char *Bimg;
     float *Bscale;
+    unsigned *Bmax;      // max |entry| bits of the operators being imaged (atomicMax)
     // decision log (Table I order): kind << 24 | pixel, and lambda or mu
     int *ev;
     float *evv;
@@ -103,6 +104,11 @@ cudaError_t launch_job(JobDev *const *jobs, int n, int max_p, int mode, DevInfo 
                        double *const *sigma_out, cudaStream_t st);
 cudaError_t launch_psi(const JobDev *job_dev, const float *wx, float2 *part, int nparts, int Q,
                        int p, int mode, double2 *Kout, cudaStream_t st);
+// Wide tensor-core adjoint (64 < p <= 256, mode 1 or 2) from U in FP32
+// (u64 false) or FP64 complex (converted while the operand image is
+// written); bmax is the job's Bmax (device), cleared here.
+cudaError_t launch_psi_adj_wide(const JobDev *job_dev, unsigned *bmax, const void *U, bool u64, double *out,
+                                int Q, int p, int mode, cudaStream_t st);
 cudaError_t launch_psi_adj(const JobDev *job_dev, const float2 *U, double *out, int Q, int p,
                            int mode, cudaStream_t st);
 cudaError_t launch_z2c(const double2 *src, float2 *dst, int n, cudaStream_t st);

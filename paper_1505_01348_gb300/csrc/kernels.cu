@@ -52,7 +52,10 @@ __device__ void factor_job(const JobDev &J) {
     const int p = J.p;
     double2 *L = J.L64;
     __shared__ int bad;
-    if (threadIdx.x == 0) bad = 0;
+    if (threadIdx.x == 0) {
+        bad = 0;
+        if (J.Bmax) J.Bmax[0] = J.Bmax[1] = 0u;   // max |R|, |R^-1| of the wide bounds start at zero
+    }
     for (int e = threadIdx.x; e < p * p; e += blockDim.x) L[e] = J.R64[e];
     __syncthreads();
     for (int j = 0; j < p; ++j) {
@@ -229,6 +232,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_psi_adj_tc(const JobDev *Jp, co
     tc_teardown(T, J.p);
 }
 
+// max |entry| of R_hat (blockIdx.y = 0) and R_hat^-1 (1) per job, 8 blocks
+// each (J.Bmax was zeroed by the factor kernel).
+__global__ void k_emb_max_bounds(JobDev *const *jobs) {
+    const JobDev &J = *jobs[blockIdx.x];
+    if (J.flags[0] != 0) return;
+    const int w = blockIdx.y;
+    emb_absmax(w ? J.Ri32 : J.R32, J.p, blockIdx.z, gridDim.z, J.Bmax + w);
+}
+
 // Chunked B images of R_hat (blockIdx.y = 0) and R_hat^-1 (1) per job; one
 // CTA per (64-column chunk, block of kEmbRows rows): blockIdx.z = chunk *
 // (512 / kEmbRows) + row block.
@@ -239,8 +251,8 @@ __global__ void k_emb_bounds(JobDev *const *jobs) {
     const int kc = blockIdx.z / kRB, rb = blockIdx.z - kc * kRB;
     if (J.flags[0] != 0 || kc >= wide_nk(J.p) || rb * kEmbRows >= 2 * wide_kp(J.p)) return;
     const int w = blockIdx.y;
-    emb_B_chunk<MODE == 2>(w ? J.Ri32 : J.R32, J.p, J.Bimg + (size_t)w * wide_B_bytes(J.p), J.Bscale + w, kc,
-                           rb);
+    emb_B_chunk<MODE == 2>(w ? J.Ri32 : J.R32, J.p, J.Bimg + (size_t)w * wide_B_bytes(J.p), J.Bmax[w],
+                           J.Bscale + w, kc, rb);
 }
 
 // Wide tensor-core bounds for 64 < p <= 256: dirty image (B = R_hat) and
@@ -263,10 +275,15 @@ __global__ void __launch_bounds__(kWideThreads, 1) k_bounds_wide(JobDev *const *
     if (to && threadIdx.x == 0) J.flags[2] = IMG_ETIMEOUT;
 }
 
-// B image of one operator U for k_psi_adj_wide; grid (chunks, row blocks).
-template <int MODE>
-__global__ void k_emb_one(const JobDev *Jp, const float2 *U) {
-    emb_B_chunk<MODE == 2>(U, Jp->p, Jp->Bimg, Jp->Bscale, blockIdx.x, blockIdx.y);
+// max |entry| of one operator U (Jp->Bmax[0] zeroed before), and its B
+// image for k_psi_adj_wide (grid: chunks x row blocks).
+template <class TC>
+__global__ void k_emb_max_one(const JobDev *Jp, const TC *U) {
+    emb_absmax(U, Jp->p, blockIdx.x, gridDim.x, Jp->Bmax);
+}
+template <int MODE, class TC>
+__global__ void k_emb_one(const JobDev *Jp, const TC *U) {
+    emb_B_chunk<MODE == 2>(U, Jp->p, Jp->Bimg, Jp->Bmax[0], Jp->Bscale, blockIdx.x, blockIdx.y);
 }
 
 // Wide tensor-core Psi^H vect(U) over all pixels of one job.
@@ -1121,6 +1138,7 @@ static cudaError_t launch_bounds_tc_t(JobDev *const *jobs, int n, int max_tiles,
 
 template <int MODE>
 static cudaError_t launch_bounds_wide_t(JobDev *const *jobs, int n, int max_tiles, int max_p, cudaStream_t st) {
+    k_emb_max_bounds<<<dim3(n, 2, 8), kThreads, 0, st>>>(jobs);
     k_emb_bounds<MODE><<<dim3(n, 2, wide_nk(max_p) * (2 * kWideMaxP / kEmbRows)), kThreads, 0, st>>>(jobs);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1231,25 +1249,39 @@ static cudaError_t launch_psi_adj_tc_t(const JobDev *job_dev, const float2 *U, d
 }
 
 template <int MODE>
-static cudaError_t launch_psi_adj_wide_t(const JobDev *job_dev, const float2 *U, double *out, int Q, int p,
-                                         cudaStream_t st) {
-    k_emb_one<MODE><<<dim3(wide_nk(p), 2 * wide_kp(p) / kEmbRows), kThreads, 0, st>>>(job_dev, U);
-    cudaError_t e = cudaGetLastError();
+static cudaError_t launch_psi_adj_wide_t(const JobDev *job_dev, unsigned *bmax, const void *U, bool u64,
+                                         double *out, int Q, int p, cudaStream_t st) {
+    const dim3 eg(wide_nk(p), 2 * wide_kp(p) / kEmbRows);
+    cudaError_t e = cudaMemsetAsync(bmax, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    const int nmax = min(16, (p * p + kThreads - 1) / kThreads);
+    if (u64) {
+        k_emb_max_one<double2><<<nmax, kThreads, 0, st>>>(job_dev, static_cast<const double2 *>(U));
+        k_emb_one<MODE, double2><<<eg, kThreads, 0, st>>>(job_dev, static_cast<const double2 *>(U));
+    } else {
+        k_emb_max_one<float2><<<nmax, kThreads, 0, st>>>(job_dev, static_cast<const float2 *>(U));
+        k_emb_one<MODE, float2><<<eg, kThreads, 0, st>>>(job_dev, static_cast<const float2 *>(U));
+    }
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t sm = wide_smem_bytes(p);
     e = ensure_smem((const void *)k_psi_adj_wide<MODE>, sm);
     if (e != cudaSuccess) return e;
-    const int ntiles = (Q + kTcM - 1) / kTcM + 64;
+    const int ntiles = (Q + kTcM - 1) / kTcM + 64;   // >= 2-D tiles of any grid
     k_psi_adj_wide<MODE><<<min(ntiles, num_sms()), kWideThreads, sm, st>>>(job_dev, out);
     return cudaGetLastError();
 }
 
+cudaError_t launch_psi_adj_wide(const JobDev *job_dev, unsigned *bmax, const void *U, bool u64, double *out,
+                                int Q, int p, int mode, cudaStream_t st) {
+    if (p <= kMaxTcP || p > kMaxWideP || (mode != 1 && mode != 2)) return cudaErrorInvalidValue;
+    if (mode == 1) return launch_psi_adj_wide_t<1>(job_dev, bmax, U, u64, out, Q, p, st);
+    return launch_psi_adj_wide_t<2>(job_dev, bmax, U, u64, out, Q, p, st);
+}
+
 cudaError_t launch_psi_adj(const JobDev *job_dev, const float2 *U, double *out, int Q, int p, int mode,
                            cudaStream_t st) {
-    if (mode != 0 && p > kMaxTcP) {
-        if (mode == 1) return launch_psi_adj_wide_t<1>(job_dev, U, out, Q, p, st);
-        return launch_psi_adj_wide_t<2>(job_dev, U, out, Q, p, st);
-    }
+    if (mode != 0 && p > kMaxTcP) return cudaErrorInvalidValue;   // wide arrays: launch_psi_adj_wide
     if (mode == 1) return launch_psi_adj_tc_t<1>(job_dev, U, out, Q, p, st);
     if (mode == 2) return launch_psi_adj_tc_t<2>(job_dev, U, out, Q, p, st);
     const size_t sm = bounds_smem_bytes(p);

@@ -130,37 +130,43 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;" ::: "memory"); }
 
 // ---------------------------------------------------------------- B image
-// Power-of-two scale that brings max |U| to (1/2, 1], computed by every CTA
-// (p^2 <= 65536 complex entries, read as float4 pairs, 8 loads in flight).
-__device__ inline float emb_scale(const float2 *U, int p) {
+__device__ __forceinline__ float2 to_f2(float2 v) { return v; }
+__device__ __forceinline__ float2 to_f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
+
+// max |Re|, |Im| over the p^2 entries of U (rounded to FP32), one block's
+// share (grid-stride over blocks `b` of `nb`), folded into *mx as the bit
+// pattern of a non-negative float (atomicMax on the bits is monotonic).
+// *mx must be zero before the first block adds to it.
+template <class TC>
+__device__ inline void emb_absmax(const TC *U, int p, int b, int nb, unsigned *mx_bits) {
     __shared__ float sred[32];
-    const int n2 = p * p, nv = n2 >> 1;
+    const int n2 = p * p, stride = nb * blockDim.x;
     float mx = 0.f;
-    if ((reinterpret_cast<uintptr_t>(U) & 15) == 0) {
-        const float4 *U4 = reinterpret_cast<const float4 *>(U);
-        int e = threadIdx.x;
-        for (; e + 7 * (int)blockDim.x < nv; e += 8 * blockDim.x) {
-            float4 v[8];
+    int e = b * blockDim.x + threadIdx.x;
+    for (; e + 3 * stride < n2; e += 4 * stride) {
+        float2 v[4];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) v[q] = U4[e + q * blockDim.x];
+        for (int q = 0; q < 4; ++q) v[q] = to_f2(U[e + q * stride]);
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-                mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v[q].x), fabsf(v[q].y)), fmaxf(fabsf(v[q].z), fabsf(v[q].w))));
-        }
-        for (; e < nv; e += blockDim.x) {
-            const float4 v = U4[e];
-            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
-        }
-        if ((n2 & 1) && threadIdx.x == 0) mx = fmaxf(mx, fmaxf(fabsf(U[n2 - 1].x), fabsf(U[n2 - 1].y)));
-    } else {
-        for (int e = threadIdx.x; e < n2; e += blockDim.x) mx = fmaxf(mx, fmaxf(fabsf(U[e].x), fabsf(U[e].y)));
+        for (int q = 0; q < 4; ++q) mx = fmaxf(mx, fmaxf(fabsf(v[q].x), fabsf(v[q].y)));
+    }
+    for (; e < n2; e += stride) {
+        const float2 v = to_f2(U[e]);
+        mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
     }
     for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = mx;
     __syncthreads();
-    mx = 0.f;
-    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) mx = fmaxf(mx, sred[w]);
-    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x + 31) / 32; ++w) mx = fmaxf(mx, sred[w]);
+        mx = fmaxf(mx, sred[0]);
+        atomicMax(mx_bits, __float_as_uint(mx));
+    }
+}
+
+// Power-of-two scale that brings max |U| to (1/2, 1].
+__device__ __forceinline__ float emb_scale_of(unsigned mx_bits) {
+    const float mx = __uint_as_float(mx_bits);
     return mx > 0.f ? exp2f(-ceilf(log2f(mx))) : 1.f;
 }
 
@@ -168,14 +174,16 @@ __device__ inline float emb_scale(const float2 *U, int p) {
 constexpr int kEmbRows = 64;
 
 // Rows [rb * kEmbRows, +kEmbRows) of chunk kc of the B image of U
-// (column-major p x p): B = emb(V), V = U^H, whose quadratic form equals
+// (column-major p x p, FP32 or FP64 complex, used as FP32): B = emb(V), V = U^H, whose quadratic form equals
 // that of emb(U).  With u = U[k_row * p + k_col] (= conj V(k_row, k_col)):
 // blocks (Re, Re) and (Im, Im) hold u.x, (Re, Im) holds u.y, (Im, Re) holds
-// -u.y.  The CTA of chunk 0, row block 0 stores the scale.
-template <bool BF16>
-__device__ void emb_B_chunk(const float2 *U, int p, unsigned char *img, float *scale, int kc, int rb) {
+// -u.y; scaled by the power of two of emb_scale_of(mx_bits) (max |U| from
+// emb_absmax).  The CTA of chunk 0, row block 0 stores the scale.
+template <bool BF16, class TC>
+__device__ void emb_B_chunk(const TC *U, int p, unsigned char *img, unsigned mx_bits, float *scale, int kc,
+                            int rb) {
     const int Kp = wide_kp(p), nc8 = Kp / 8, nu = wide_units(p), rows_u = wide_unit_rows(p);
-    const float sc = emb_scale(U, p);
+    const float sc = emb_scale_of(mx_bits);
     if (kc == 0 && rb == 0 && threadIdx.x == 0) *scale = sc;
     unsigned char *chunk = img + (size_t)kc * wide_chunk_bytes(p);
     const size_t ub = wide_unit_bytes(p);
@@ -189,7 +197,7 @@ __device__ void emb_B_chunk(const float2 *U, int p, unsigned char *img, float *s
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             float2 u = make_float2(0.f, 0.f);
-            if (kr < p && k0 + e < p) u = U[(size_t)kr * p + k0 + e];
+            if (kr < p && k0 + e < p) u = to_f2(U[(size_t)kr * p + k0 + e]);
             const float val = (rpart == cpart) ? u.x : (rpart == 0 ? u.y : -u.y);
             v[e] = val * sc;
         }
