@@ -228,13 +228,15 @@ def run_ours(args, rank: int, world: int):
 
 # ---------------------------------------------------------------- serving
 def run_operators(args, ps=(128, 256), n: int = 256, reps: int = 20):
-    """Adjoint operator Psi^H (Eq. 16) on wide arrays, full 256x256 grid:
-    the streamed tensor-core kernel (64 < p <= 256).  Each call reduces
+    """Operator pair on wide arrays (64 < p <= 256), full 256x256 grid.
+    Adjoint Psi^H (Eq. 16): the streamed tensor-core kernel; each call reduces
     max |U|, writes the chunked operand image from the complex128 U and runs
     the adjoint; calls are queued back to back on one stream and timed with
     CUDA events.
     Useful flops: 8 p^2 Q; issued: the three split products on the padded
-    2Kp x 2Kp operand, 3 * 2 * 128 * (2Kp)^2 per 128-pixel tile."""
+    2Kp x 2Kp operand, 3 * 2 * 128 * (2Kp)^2 per 128-pixel tile.  Forward
+    Psi x (Eq. 15) as tensor-core Gram blocks: useful 4 p^2 Q (Hermitian
+    half), issued 3 * 2 * 128 * N per pixel for every 128 x N block formed."""
     import torch
     import paper_1505_01348_gb300 as G
     import synth
@@ -244,8 +246,11 @@ def run_operators(args, ps=(128, 256), n: int = 256, reps: int = 20):
         return None
     pk = measured_peaks()
     peak = float(pk.get("bf16_tflops") or 1900.0)
-    out_d = {"kernel": "k_psi_adj_wide", "grid": f"{n}x{n}", "precision": args.precision,
-             "per_call": "max |U| reduction + operand image + adjoint (U read in place)", "peak_tflops": peak,
+    out_d = {"grid": f"{n}x{n}", "precision": args.precision,
+             "kernels": "k_psi_adj_wide (adjoint), k_fwd_wide (forward)",
+             "per_call": ("adjoint: max |U| reduction + operand image + adjoint (U read in place); forward: "
+                          "FP32 weights + max |w| + Gram blocks + ordered partial sums into K"),
+             "peak_tflops": peak,
              "peak_basis": "measured dense BF16 burst (FP16 runs at the BF16 rate)"}
     st = torch.cuda.Stream()
     for p in ps:
@@ -270,8 +275,31 @@ def run_operators(args, ps=(128, 256), n: int = 256, reps: int = 20):
         tiles = ((n + 7) // 8) * ((n + 15) // 16)
         useful = 8.0 * p * p * job.Q
         issued = 3 * 2.0 * 128 * (2 * kp) ** 2 * tiles
-        out_d[f"p{p}"] = {"us_per_call": t * 1e6, "useful_tflops": useful / t / 1e12,
-                          "issued_tflops": issued / t / 1e12, "issued_frac": issued / t / 1e12 / peak}
+        rec = {"adjoint_us_per_call": t * 1e6, "adjoint_useful_tflops": useful / t / 1e12,
+               "adjoint_issued_tflops": issued / t / 1e12, "adjoint_issued_frac": issued / t / 1e12 / peak}
+        # forward Psi x (Gram blocks of 128 x <=256 features over 64-pixel stages)
+        x = torch.rand(job.Q, dtype=torch.float64, device="cuda")
+        K = torch.empty((p, p), dtype=torch.complex128, device="cuda")
+        im2 = G.Imager.from_job(job, precision=prec, stream=st.cuda_stream)
+        for _ in range(3):
+            im2.psi(x, K)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(reps):
+            im2.psi(x, K, wait=False)
+        e1.record(st)
+        torch.cuda.synchronize()
+        tf = e0.elapsed_time(e1) / 1e3 / reps
+        im2.close()
+        nf = 2 * kp
+        blocks = [(m, nb) for m in range((nf + 127) // 128) for nb in range((nf + 255) // 256)
+                  if 256 * nb + min(256, nf - 256 * nb) - 1 >= 128 * m]
+        pix = ((n + 7) // 8) * ((n + 7) // 8) * 64
+        fissued = sum(3 * 2.0 * 128 * min(256, nf - 256 * nb) * pix for _, nb in blocks)
+        fuseful = 4.0 * p * p * job.Q
+        rec.update({"forward_us_per_call": tf * 1e6, "forward_useful_tflops": fuseful / tf / 1e12,
+                    "forward_issued_tflops": fissued / tf / 1e12, "forward_issued_frac": fissued / tf / 1e12 / peak})
+        out_d[f"p{p}"] = rec
     return out_d
 
 

@@ -36,6 +36,7 @@ struct img_ctx {
     float2 *U32 = nullptr;
     double2 *Z = nullptr;        // p*p complex128 staging
     double *outd = nullptr;      // Q doubles staging
+    float *fwd_part = nullptr;   // partial Gram blocks of the wide forward (allocated on first use)
 };
 
 namespace {
@@ -477,7 +478,19 @@ img_status img_psi(img_ctx *c, const double *x, double *Kout, int on_device) {
         CK(cudaMemcpyAsync(c->wx, f.data(), Q * sizeof(float), cudaMemcpyHostToDevice, c->stream));
         CK(cudaStreamSynchronize(c->stream));
     }
-    CK(img::launch_psi(c->dj, c->wx, c->part, c->nparts, Q, p, mode_of(c), c->Z, c->stream));
+    const int om = op_mode_of(c);
+    if (om != 0 && p > img::kMaxTcP) {
+        // tensor-core Gram blocks; their partial sums need a scratch buffer
+        if (!c->fwd_part) {
+            int sms = 1;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+            CK(cudaMalloc(&c->fwd_part, img::psi_wide_part_floats(sms) * sizeof(float)));
+        }
+        CK(img::launch_psi_wide(c->dj, c->hj.Bmax + 1, c->wx, c->fwd_part, Q, p, c->prm.n_l, c->prm.n_m, om, c->Z,
+                                c->stream));
+    } else {
+        CK(img::launch_psi(c->dj, c->wx, c->part, c->nparts, Q, p, mode_of(c), c->Z, c->stream));
+    }
     CK(cudaMemcpyAsync(Kout, c->Z, (size_t)p * p * sizeof(double2),
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
     if (on_device == 2) return IMG_OK;           // stream-ordered, no host wait
@@ -665,6 +678,7 @@ void img_destroy(img_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->dmem) cudaFree(c->dmem);
+    if (c->fwd_part) cudaFree(c->fwd_part);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }

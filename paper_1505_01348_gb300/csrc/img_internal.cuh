@@ -104,6 +104,12 @@ cudaError_t launch_job(JobDev *const *jobs, int n, int max_p, int mode, DevInfo 
                        double *const *sigma_out, cudaStream_t st);
 cudaError_t launch_psi(const JobDev *job_dev, const float *wx, float2 *part, int nparts, int Q,
                        int p, int mode, double2 *Kout, cudaStream_t st);
+// Wide tensor-core forward K = Psi w (64 < p <= 256, mode 1 or 2): wbits is
+// a device word (cleared here), part a scratch of psi_wide_part_floats(SMs)
+// floats; Kout p x p complex128.
+size_t psi_wide_part_floats(int sms);
+cudaError_t launch_psi_wide(const JobDev *job_dev, unsigned *wbits, const float *wx, float *part, int Q, int p,
+                            int n_l, int n_m, int mode, double2 *Kout, cudaStream_t st);
 // Wide tensor-core adjoint (64 < p <= 256, mode 1 or 2) from U in FP32
 // (u64 false) or FP64 complex (converted while the operand image is
 // written); bmax is the job's Bmax (device), cleared here.

@@ -301,6 +301,73 @@ __global__ void __launch_bounds__(kWideThreads, 1) k_psi_adj_wide(const JobDev *
                             [&](int, int i, float v) { out[i] = v; });
 }
 
+// ---------------------------------------------------------------- wide forward
+// Blocks of G formed by k_fwd_wide, in fwd_pairs order, and the index of
+// block (m, nb) in that order (-1: not formed).
+struct FwdMap {
+    int np;
+    int m[8], nb[8];
+    int idx[4][2];
+};
+
+__global__ void k_fwd_wmax(const float *w, int Q, unsigned *wbits) { fwd_wmax(w, Q, wbits); }
+
+template <int MODE>
+__global__ void __launch_bounds__(kFwdThreads, 1) k_fwd_wide(const JobDev *Jp, const float *w, const unsigned *wbits,
+                                                            FwdMap map, float *part) {
+    const JobDev &J = *Jp;
+    extern __shared__ float4 smem4[];
+    unsigned char *dyn = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem4) + 1023) & ~uintptr_t(1023));
+    __shared__ uint64_t bars[5];
+    __shared__ uint32_t slot;
+    const int pr = blockIdx.y, S = gridDim.x;
+    wide_forward<MODE == 2>(J, dyn, bars, &slot, w, *wbits, map.m[pr], map.nb[pr], blockIdx.x, S,
+                            part + ((size_t)pr * S + blockIdx.x) * (kTcM * 256));
+}
+
+// Sum of the S partials of every formed block, in a fixed order: 4 groups
+// of threads take s = g, g + 4, ... for 64 consecutive entries, then the 4
+// group sums are added in group order.  Ub: np blocks of 128 x 256 doubles.
+__global__ void k_fwd_reduce(const float *part, int S, int nent, double *Ub) {
+    __shared__ double red[4][64];
+    const int j = threadIdx.x & 63, g = threadIdx.x >> 6;
+    const int e = blockIdx.x * 64 + j;
+    constexpr size_t kBlk = (size_t)kTcM * 256;
+    double acc = 0.0;
+    if (e < nent) {
+        const int pr = e / (int)kBlk, off = e - pr * (int)kBlk;
+        const float *q = part + (size_t)pr * S * kBlk + off;
+#pragma unroll 4
+        for (int s = g; s < S; s += 4) acc += q[(size_t)s * kBlk];
+    }
+    red[g][j] = acc;
+    __syncthreads();
+    if (g == 0 && e < nent) Ub[e] = ((red[0][j] + red[1][j]) + red[2][j]) + red[3][j];
+}
+
+// K (p x p complex128, column-major) from the summed blocks: entries of G on
+// or above the diagonal, U(a, b); K_kl = U(k,l) + U(Kp+k,Kp+l) + j (U(l,Kp+k)
+// - U(k,Kp+l)) for k <= l, scaled back by 1 / (sX^2 sW); K_lk = conj(K_kl).
+__global__ void k_fwd_assemble(int p, const double *Ub, FwdMap map, const unsigned *wbits, double2 *K) {
+    const int Kp = wide_kp(p);
+    const float sX = steer_scale(p);
+    const double inv = 1.0 / ((double)sX * sX * emb_scale_of(*wbits));
+    constexpr size_t kBlk = (size_t)kTcM * 256;
+    auto U = [&](int a, int b) {
+        const int m = a >> 7, nb = b >> 8, pr = map.idx[m][nb];
+        return Ub[(size_t)pr * kBlk + (size_t)(a - 128 * m) * 256 + (b - 256 * nb)];
+    };
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p * p; e += gridDim.x * blockDim.x) {
+        const int l = e / p, k = e - l * p;
+        if (k > l) continue;
+        const double re = (U(k, l) + U(Kp + k, Kp + l)) * inv;
+        const double im = k == l ? 0.0 : (U(l, Kp + k) - U(k, Kp + l)) * inv;
+        K[(size_t)l * p + k] = make_double2(re, im);
+        K[(size_t)k * p + l] = make_double2(re, -im);
+    }
+}
+
 // Bounds, preconditioner and thresholds (one CTA per job):
 //   C = N/(N-p) or 1; mvdr = C/h; D = h^2/C; std_MF = dirty/sqrt(N);
 //   std_MVDR = mvdr/sqrt(N-p-1); gamma = chosen image, optionally inflated;
@@ -1234,6 +1301,40 @@ cudaError_t launch_psi(const JobDev *job_dev, const float *wx, float2 *part, int
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_psi_reduce<<<(p * p + 255) / 256, 256, 0, st>>>(part, used, p * p, Kout);
+    return cudaGetLastError();
+}
+
+// Partial blocks (one per CTA, at most one CTA per SM) followed by the
+// summed blocks (at most 6, in doubles).
+size_t psi_wide_part_floats(int sms) { return (size_t)sms * kTcM * 256 + (size_t)2 * 8 * kTcM * 256; }
+
+cudaError_t launch_psi_wide(const JobDev *job_dev, unsigned *wbits, const float *wx, float *part, int Q, int p,
+                            int n_l, int n_m, int mode, double2 *Kout, cudaStream_t st) {
+    if (p <= kMaxTcP || p > kMaxWideP || (mode != 1 && mode != 2)) return cudaErrorInvalidValue;
+    FwdMap map{};
+    map.np = fwd_pairs(p, map.m, map.nb);
+    for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 2; ++b) map.idx[a][b] = -1;
+    for (int q = 0; q < map.np; ++q) map.idx[map.m[q]][map.nb[q]] = q;
+    const int sms = num_sms();
+    const int nblk = fwd_nblocks(n_l, n_m);
+    const int S = max(1, min(nblk, sms / map.np));
+    cudaError_t e = cudaMemsetAsync(wbits, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    k_fwd_wmax<<<max(1, min(2 * sms, (Q + 4 * kThreads - 1) / (4 * kThreads))), kThreads, 0, st>>>(wx, Q, wbits);
+    const size_t sm = fwd_smem_bytes();
+    e = (mode == 1) ? ensure_smem((const void *)k_fwd_wide<1>, sm) : ensure_smem((const void *)k_fwd_wide<2>, sm);
+    if (e != cudaSuccess) return e;
+    if (mode == 1)
+        k_fwd_wide<1><<<dim3(S, map.np), kFwdThreads, sm, st>>>(job_dev, wx, wbits, map, part);
+    else
+        k_fwd_wide<2><<<dim3(S, map.np), kFwdThreads, sm, st>>>(job_dev, wx, wbits, map, part);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    double *Ub = reinterpret_cast<double *>(part + (size_t)sms * kTcM * 256);
+    const int nent = map.np * kTcM * 256;
+    k_fwd_reduce<<<(nent + 63) / 64, 256, 0, st>>>(part, S, nent, Ub);
+    k_fwd_assemble<<<(p * p + kThreads - 1) / kThreads, kThreads, 0, st>>>(p, Ub, map, wbits, Kout);
     return cudaGetLastError();
 }
 

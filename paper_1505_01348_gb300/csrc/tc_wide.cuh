@@ -505,4 +505,275 @@ __device__ int wide_adjoint(const JobDev &J, unsigned char *dyn, uint64_t *bars,
     return s_timeouts;
 }
 
+
+// ================================================================ forward
+// Psi x for 64 < p <= 256 on tensor cores: K = sum_i w_i a_i a_i^H from the
+// real Gram matrix G = sum_i w_i x_i x_i^T (2Kp x 2Kp), K = (G_rr + G_ii) +
+// j (G_ir - G_ri).  G is tiled in blocks of 128 rows (features 128m ..) by up
+// to 256 columns (features 256nb ..); only blocks that reach the upper
+// triangle are formed.  One CTA accumulates one block over a strided share
+// of 64-pixel stages (8 x 8 grid blocks) with the pixel index as the MMA's K
+// dimension: both operands are pixel-major tiles read as MN-major operands
+// (the same swizzled layout the adjoint's steering tiles use), A unweighted
+// and B weighted by w_i, split hi + lo as in the adjoint.  Each CTA writes its
+// FP32 block to a partial buffer; fwd_assemble sums the partials in a fixed
+// order (deterministic) and forms K.
+//   warps 0-7  steering producers (then warps 0-3 read the accumulator);
+//   warp 8     MMA issue (lane 0).
+constexpr int kFwdPix = 64;                                  // pixels per stage
+constexpr size_t kFwdChunk = (size_t)kFwdPix * 128;          // one 64-feature chunk, 8 KB
+constexpr size_t kFwdStage = (2 + 4) * 2 * kFwdChunk;        // A: 2 chunks, B: 4 chunks, hi + lo
+constexpr int kFwdThreads = 288;
+__host__ __device__ inline size_t fwd_smem_bytes() { return 2 * kFwdStage + 1024; }
+__host__ __device__ inline int fwd_n_of(int p, int nb) {
+    const int n = 2 * wide_kp(p) - 256 * nb;
+    return n < 256 ? n : 256;
+}
+// Blocks (m, nb) of G that reach the upper triangle, in a fixed order.
+__host__ __device__ inline int fwd_pairs(int p, int *pm, int *pnb) {
+    const int N = 2 * wide_kp(p), nm = (N + 127) / 128, nnb = (N + 255) / 256;
+    int k = 0;
+    for (int m = 0; m < nm; ++m)
+        for (int nb = 0; nb < nnb; ++nb)
+            if (256 * nb + fwd_n_of(p, nb) - 1 >= 128 * m) {
+                if (pm) pm[k] = m;
+                if (pnb) pnb[k] = nb;
+                ++k;
+            }
+    return k;
+}
+__host__ __device__ inline int fwd_nblocks(int n_l, int n_m) { return ((n_l + 7) / 8) * ((n_m + 7) / 8); }
+
+// Instruction descriptor, kind::f16, F32 accumulate, both operands MN-major,
+// M = 128, N = n.
+__host__ __device__ constexpr uint32_t idesc_f16_mn128(int n, int ab_fmt) {
+    return (1u << 4) | ((uint32_t)ab_fmt << 7) | ((uint32_t)ab_fmt << 10) | (1u << 15) | (1u << 16) |
+           ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+}
+
+// max |w| over Q weights (block share of a grid-stride pass), into *mx_bits.
+__device__ inline void fwd_wmax(const float *w, int Q, unsigned *mx_bits) {
+    __shared__ float sred[32];
+    float mx = 0.f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Q; i += gridDim.x * blockDim.x) mx = fmaxf(mx, fabsf(w[i]));
+    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < (int)(blockDim.x + 31) / 32; ++q) mx = fmaxf(mx, sred[q]);
+        mx = fmaxf(mx, sred[0]);
+        atomicMax(mx_bits, __float_as_uint(mx));
+    }
+}
+
+// One CTA: block `pair` of G over the pixel blocks s, s + S, ... of the grid;
+// writes the FP32 block (128 x 256, row-major) to out.  w: pixel weights;
+// wbits: max |w| bits.  Returns the number of waits that timed out.
+template <bool BF16>
+__device__ int wide_forward(const JobDev &J, unsigned char *dyn, uint64_t *bars, uint32_t *slot, const float *w,
+                            unsigned wbits, int m, int nb, int s0, int S, float *out) {
+    const int p = J.p, Kp = wide_kp(p), Nf = 2 * Kp, N = fwd_n_of(p, nb);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nl = J.n_l, nm = J.n_m, tlb = (nl + 7) / 8, nblk = fwd_nblocks(nl, nm);
+    const int mine = nblk > s0 ? (nblk - 1 - s0) / S + 1 : 0;
+    const float sX = steer_scale(p);
+    const float sW = emb_scale_of(wbits);
+    enum { kFull = 0, kEmpty = 2, kAcc = 4 };
+    __shared__ int s_timeouts;
+    if (threadIdx.x == 0) {
+        s_timeouts = 0;
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&bars[kFull + q], 8);
+            mbar_init(&bars[kEmpty + q], 1);
+        }
+        mbar_init(&bars[kAcc], 1);
+    }
+    if (warp == 0) tmem_alloc(slot, 256);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *slot;
+    int timeouts = 0;
+    uint32_t ph = 0;
+    // chunks of features: A = {2m, 2m+1}, B = {4nb .. 4nb+3}; chunk list without repeats
+    int chunk[6], nchunk = 0;
+    for (int q = 0; q < 2; ++q) chunk[nchunk++] = 2 * m + q;
+    for (int q = 0; q < 4; ++q) {
+        const int c = 4 * nb + q;
+        if (64 * c < 256 * nb + N && c != 2 * m && c != 2 * m + 1) chunk[nchunk++] = c;
+    }
+
+    if (warp == 8) {
+        if (lane == 0 && mine > 0) {
+            const uint32_t idesc = idesc_f16_mn128(N, BF16 ? 1 : 0);
+            for (int t = 0; t < mine; ++t) {
+                const int sg = t & 1;
+                wide_wait(bars, kFull + sg, ph, timeouts);
+                tc_fence_after();
+                const uint32_t base = smem_u32(dyn + sg * kFwdStage);
+                const uint32_t ah = base, al = base + 2 * kFwdChunk;
+                const uint32_t bh = base + 4 * kFwdChunk, bl = base + 8 * kFwdChunk;
+#pragma unroll
+                for (int st = 0; st < kFwdPix / 16; ++st) {
+                    const uint32_t o = st * 2048;
+                    const uint32_t acc = (t > 0 || st > 0) ? 1u : 0u;
+                    mma_f16(tmem, sw128_desc_mn(ah + o, kFwdChunk, 1024), sw128_desc_mn(bh + o, kFwdChunk, 1024),
+                            idesc, acc);
+                    mma_f16(tmem, sw128_desc_mn(ah + o, kFwdChunk, 1024), sw128_desc_mn(bl + o, kFwdChunk, 1024),
+                            idesc, 1u);
+                    mma_f16(tmem, sw128_desc_mn(al + o, kFwdChunk, 1024), sw128_desc_mn(bh + o, kFwdChunk, 1024),
+                            idesc, 1u);
+                }
+                mma_commit(&bars[kEmpty + sg]);
+                if (t == mine - 1) mma_commit(&bars[kAcc]);
+            }
+        }
+    } else {
+        // ---------------- producers: warp w takes tasks (chunk, half h) w, w + 8, ...
+        // of each stage: the 32 pixel rows of m offsets b = 4h .. 4h+3 (l offsets
+        // a = 0..7), lane j the features 2j, 2j+1 of the chunk.  The 8 E_l and
+        // 4 E_m entries and the lane's weight of the warp's next task (in this
+        // stage or the next) load while the current task is written.
+        const bool vec = (p & 1) == 0;
+        const float2 *__restrict__ El = J.El;
+        const float2 *__restrict__ Em = J.Em;
+        const int ntask = nchunk * 2;
+        const int my = warp < ntask ? (ntask - 1 - warp) / 8 + 1 : 0;    // tasks per stage
+        float2 e[8][2], fm[4][2];
+        float wl = 0.f;
+        auto load = [&](int t, int task) {
+            const int blk = s0 + t * S, bm = blk / tlb, bl = blk - bm * tlb;
+            const int ci = task >> 1, h = task & 1, c = chunk[ci];
+            const int f = c * 64 + 2 * lane, part = f >= Kp, k = f - part * Kp;
+            const bool kok = f < Nf && k < p;
+#pragma unroll
+            for (int a = 0; a < 8; ++a) {
+                const int il = bl * 8 + a;
+                e[a][0] = e[a][1] = make_float2(0.f, 0.f);
+                if (kok && il < nl) {
+                    const float2 *src = El + (size_t)il * p + k;
+                    if (vec) {
+                        const float4 v = __ldg(reinterpret_cast<const float4 *>(src));
+                        e[a][0] = make_float2(v.x, v.y);
+                        e[a][1] = make_float2(v.z, v.w);
+                    } else {
+                        e[a][0] = __ldg(src);
+                        if (k + 1 < p) e[a][1] = __ldg(src + 1);
+                    }
+                }
+            }
+#pragma unroll
+            for (int bb = 0; bb < 4; ++bb) {
+                const int im = bm * 8 + 4 * h + bb;
+                fm[bb][0] = fm[bb][1] = make_float2(0.f, 0.f);
+                if (kok && im < nm) {
+                    const float2 *src = Em + (size_t)im * p + k;
+                    if (vec) {
+                        const float4 v = __ldg(reinterpret_cast<const float4 *>(src));
+                        fm[bb][0] = make_float2(v.x, v.y);
+                        fm[bb][1] = make_float2(v.z, v.w);
+                    } else {
+                        fm[bb][0] = __ldg(src);
+                        if (k + 1 < p) fm[bb][1] = __ldg(src + 1);
+                    }
+                }
+            }
+            wl = 0.f;
+            const int il = bl * 8 + (lane & 7), im = bm * 8 + 4 * h + (lane >> 3);
+            if (il < nl && im < nm) wl = __ldg(w + (size_t)im * nl + il) * sW;
+        };
+        if (mine > 0 && my > 0) load(0, warp);
+        for (int t = 0; t < mine; ++t) {
+            const int sg = t & 1;
+            if (t >= 2) wide_wait(bars, kEmpty + sg, ph, timeouts);
+            unsigned char *st = dyn + sg * kFwdStage;
+            for (int q = 0; q < my; ++q) {
+                const int task = warp + 8 * q;
+                const int ci = task >> 1, h = task & 1, c = chunk[ci];
+                const int f = c * 64 + 2 * lane, part = f >= Kp;
+                float2 ec[8][2], fc[4][2];
+#pragma unroll
+                for (int a = 0; a < 8; ++a) {
+                    ec[a][0] = e[a][0];
+                    ec[a][1] = e[a][1];
+                }
+#pragma unroll
+                for (int bb = 0; bb < 4; ++bb) {
+                    fc[bb][0] = fm[bb][0];
+                    fc[bb][1] = fm[bb][1];
+                }
+                const float wc = wl;
+                // prefetch the next task of this warp
+                if (q + 1 < my) load(t, task + 8);
+                else if (t + 1 < mine) load(t + 1, warp);
+                // fold the part and sX into the E_m factors
+#pragma unroll
+                for (int bb = 0; bb < 4; ++bb)
+#pragma unroll
+                    for (int qq = 0; qq < 2; ++qq) {
+                        const float2 v = fc[bb][qq];
+                        fc[bb][qq] = part ? make_float2(v.y * sX, v.x * sX) : make_float2(v.x * sX, -v.y * sX);
+                    }
+                const bool inA = c == 2 * m || c == 2 * m + 1;
+                const bool inB = c >= 4 * nb && 64 * c < 256 * nb + N;
+                unsigned char *ah = st + (size_t)(c - 2 * m) * kFwdChunk;
+                unsigned char *bh = st + 4 * kFwdChunk + (size_t)(c - 4 * nb) * kFwdChunk;
+#pragma unroll
+                for (int bb = 0; bb < 4; ++bb) {
+#pragma unroll
+                    for (int a = 0; a < 8; ++a) {
+                        const int r = 8 * (4 * h + bb) + a;
+                        const float wi = __shfl_sync(0xffffffffu, wc, bb * 8 + a);
+                        const float v0 = fmaf(ec[a][0].x, fc[bb][0].x, ec[a][0].y * fc[bb][0].y);
+                        const float v1 = fmaf(ec[a][1].x, fc[bb][1].x, ec[a][1].y * fc[bb][1].y);
+                        const uint32_t off = (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 +
+                                                        (((lane >> 2) ^ (r & 7)) << 4) + (lane & 3) * 4);
+                        uint32_t hi, lo;
+                        if (inA) {
+                            split2<BF16>(v0, v1, hi, lo);
+                            *reinterpret_cast<uint32_t *>(ah + off) = hi;
+                            *reinterpret_cast<uint32_t *>(ah + 2 * kFwdChunk + off) = lo;
+                        }
+                        if (inB) {
+                            split2<BF16>(v0 * wi, v1 * wi, hi, lo);
+                            *reinterpret_cast<uint32_t *>(bh + off) = hi;
+                            *reinterpret_cast<uint32_t *>(bh + 4 * kFwdChunk + off) = lo;
+                        }
+                    }
+                }
+            }
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars[kFull + sg]);
+        }
+        // ---------------- accumulator -> out (warps 0-3: one row of the block per thread)
+        if (warp < 4) {
+            const int r = 32 * warp + lane;
+            float *row = out + (size_t)r * 256;
+            if (mine > 0) {
+                wide_wait(bars, kAcc, ph, timeouts);
+                tc_fence_after();
+                const uint32_t base = tmem + ((uint32_t)(32 * warp) << 16);
+                for (int c0 = 0; c0 < N; c0 += 32) {
+                    float d0[16], d1[16];
+                    tmem_ld16x2(base + c0, base + c0 + 16, d0, d1);
+#pragma unroll
+                    for (int q = 0; q < 16; q += 4) {
+                        *reinterpret_cast<float4 *>(row + c0 + q) = make_float4(d0[q], d0[q + 1], d0[q + 2], d0[q + 3]);
+                        *reinterpret_cast<float4 *>(row + c0 + 16 + q) =
+                            make_float4(d1[q], d1[q + 1], d1[q + 2], d1[q + 3]);
+                    }
+                }
+            } else {
+                for (int c0 = 0; c0 < N; ++c0) row[c0] = 0.f;
+            }
+        }
+    }
+    if (timeouts) atomicAdd(&s_timeouts, timeouts);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 256);
+    return s_timeouts;
+}
+
 }  // namespace img

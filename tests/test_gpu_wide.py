@@ -5,6 +5,8 @@ chunk) against the definitions, evaluated directly in FP64.
 * dirty image d_i = a_i^H R a_i and MVDR bound C / (a_i^H R^-1 a_i)
   (Sec. IV-A, Eq. 24), every pixel, ragged tiles and p not a multiple of 8;
 * Psi^H vect(U) = Re diag(A^H U A) (Eq. 16) for a random Hermitian U;
+* Psi x = vect(A diag(x) A^H) (Eq. 15, the tensor-core Gram-block forward)
+  for signed, sparse and wide-range x;
 * a solve whose bounds come from this operator (solver on CUDA cores) against
   the oracle image;
 * one batch mixing wide and narrow arrays equals the jobs run one by one.
@@ -77,6 +79,29 @@ def test_wide_psi_adjoint(G, p, prec):
     assert _rel(y, ref) <= PREC_TOL[prec]
     lhs = np.real(np.vdot(O.vect(K), O.vect(U)))
     assert abs(lhs - float(x @ y)) <= PREC_TOL[prec] * np.linalg.norm(K) * np.linalg.norm(U)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("p,nl,nm", [(65, 21, 13), (96, 24, 20), (128, 16, 16), (200, 17, 11), (256, 20, 12)])
+@pytest.mark.parametrize("kind", ["signed", "sparse", "range"])
+def test_wide_forward(G, p, nl, nm, prec, kind):
+    job = synth.custom(900 + p, p, nl, nm, 2, 4 * p + 100, radius=6.0)
+    A = O.steering_matrix(job.ant_xyz, job.l, job.m, job.lam)
+    rng = np.random.default_rng(p + nl)
+    if kind == "signed":
+        x = rng.standard_normal(job.Q)
+    elif kind == "sparse":
+        x = np.zeros(job.Q)
+        idx = rng.choice(job.Q, 7, replace=False)
+        x[idx] = rng.uniform(0.5, 2.0, 7)
+    else:
+        x = 10.0 ** rng.uniform(-4, 2, job.Q)
+    im = G.Imager.from_job(job, precision=prec)
+    K = im.psi(x)
+    im.close()
+    ref = (A * x[None, :]) @ A.conj().T
+    assert _rel(K, ref) <= PREC_TOL[prec]
+    np.testing.assert_allclose(K, K.conj().T, rtol=0, atol=1e-12 * np.abs(ref).max())
 
 
 @pytest.mark.parametrize("cost", [0, 1])
