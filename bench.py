@@ -227,8 +227,9 @@ def run_ours(args, rank: int, world: int):
 
 
 # ---------------------------------------------------------------- serving
-def run_operators(args, ps=(128, 256), n: int = 256, reps: int = 20):
-    """Operator pair on wide arrays (64 < p <= 256), full 256x256 grid.
+def run_operators(args, cases=((128, 256), (256, 256), (256, 512)), reps: int = 20):
+    """Operator pair on wide arrays (64 < p <= 256) on full n x n grids
+    (256x256 as in the serving mix, and 512x512 at p = 256).
     Adjoint Psi^H (Eq. 16): the streamed tensor-core kernel; each call reduces
     max |U|, writes the chunked operand image from the complex128 U and runs
     the adjoint; calls are queued back to back on one stream and timed with
@@ -246,14 +247,14 @@ def run_operators(args, ps=(128, 256), n: int = 256, reps: int = 20):
         return None
     pk = measured_peaks()
     peak = float(pk.get("bf16_tflops") or 1900.0)
-    out_d = {"grid": f"{n}x{n}", "precision": args.precision,
+    out_d = {"grids": "n x n pixels per case (key p<p>_<n>)", "precision": args.precision,
              "kernels": "k_psi_adj_wide (adjoint), k_fwd_wide (forward)",
              "per_call": ("adjoint: max |U| reduction + operand image + adjoint (U read in place); forward: "
                           "FP32 weights + max |w| + Gram blocks + ordered partial sums into K"),
              "peak_tflops": peak,
              "peak_basis": "measured dense BF16 burst (FP16 runs at the BF16 rate)"}
     st = torch.cuda.Stream()
-    for p in ps:
+    for p, n in cases:
         job = synth.custom(7000 + p, p, n, n, 20, 10_000, radius=50.0)
         # the context works on this stream, so events recorded on it bracket the calls
         im = G.Imager.from_job(job, precision=prec, stream=st.cuda_stream)
@@ -299,7 +300,7 @@ def run_operators(args, ps=(128, 256), n: int = 256, reps: int = 20):
         fuseful = 4.0 * p * p * job.Q
         rec.update({"forward_us_per_call": tf * 1e6, "forward_useful_tflops": fuseful / tf / 1e12,
                     "forward_issued_tflops": fissued / tf / 1e12, "forward_issued_frac": fissued / tf / 1e12 / peak})
-        out_d[f"p{p}"] = rec
+        out_d[f"p{p}_{n}"] = rec
     return out_d
 
 

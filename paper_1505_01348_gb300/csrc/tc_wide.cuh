@@ -20,6 +20,8 @@
 //   Kp > 128 each tile spans both regions (B rows split in two units) and a
 //   region is handed back as soon as the epilogue has read it.
 #pragma once
+#include <type_traits>
+
 #include "tc_ops.cuh"
 
 namespace img {
@@ -632,15 +634,19 @@ __device__ int wide_forward(const JobDev &J, unsigned char *dyn, uint64_t *bars,
         // ---------------- producers: warp w takes tasks (chunk, half h) w, w + 8, ...
         // of each stage: the 32 pixel rows of m offsets b = 4h .. 4h+3 (l offsets
         // a = 0..7), lane j the features 2j, 2j+1 of the chunk.  The 8 E_l and
-        // 4 E_m entries and the lane's weight of the warp's next task (in this
+        // 4 E_m entries and the 32 weights of the warp's next task (in this
         // stage or the next) load while the current task is written.
-        const bool vec = (p & 1) == 0;
+        const bool vec = (p & 1) == 0, wvec = (nl & 3) == 0;
         const float2 *__restrict__ El = J.El;
         const float2 *__restrict__ Em = J.Em;
         const int ntask = nchunk * 2;
         const int my = warp < ntask ? (ntask - 1 - warp) / 8 + 1 : 0;    // tasks per stage
+        // swizzled byte offset of (row a, this lane's column pair) in an 8-row group
+        uint32_t xo[8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) xo[a] = (uint32_t)(a * 128 + (((lane >> 2) ^ a) << 4) + (lane & 3) * 4);
         float2 e[8][2], fm[4][2];
-        float wl = 0.f;
+        float wr[4][8];
         auto load = [&](int t, int task) {
             const int blk = s0 + t * S, bm = blk / tlb, bl = blk - bm * tlb;
             const int ci = task >> 1, h = task & 1, c = chunk[ci];
@@ -677,10 +683,54 @@ __device__ int wide_forward(const JobDev &J, unsigned char *dyn, uint64_t *bars,
                         if (k + 1 < p) fm[bb][1] = __ldg(src + 1);
                     }
                 }
+                // the 8 weights of this m row (same address in every lane)
+                const int il0 = bl * 8;
+                const float *wrow = w + (size_t)im * nl + il0;
+                if (im < nm && wvec && il0 + 8 <= nl) {
+                    const float4 w0 = __ldg(reinterpret_cast<const float4 *>(wrow));
+                    const float4 w1 = __ldg(reinterpret_cast<const float4 *>(wrow) + 1);
+                    wr[bb][0] = w0.x; wr[bb][1] = w0.y; wr[bb][2] = w0.z; wr[bb][3] = w0.w;
+                    wr[bb][4] = w1.x; wr[bb][5] = w1.y; wr[bb][6] = w1.z; wr[bb][7] = w1.w;
+                } else {
+#pragma unroll
+                    for (int a = 0; a < 8; ++a) wr[bb][a] = (im < nm && il0 + a < nl) ? __ldg(wrow + a) : 0.f;
+                }
             }
-            wl = 0.f;
-            const int il = bl * 8 + (lane & 7), im = bm * 8 + 4 * h + (lane >> 3);
-            if (il < nl && im < nm) wl = __ldg(w + (size_t)im * nl + il) * sW;
+        };
+        // write one task: rows of m offsets 4h + bb; A (unweighted) and/or B (weighted) copies
+        auto emit = [&](unsigned char *st, int c, int h, int part, auto inA_t, auto inB_t) {
+            constexpr bool inA = decltype(inA_t)::value, inB = decltype(inB_t)::value;
+            unsigned char *ah = st + (size_t)(c - 2 * m) * kFwdChunk + h * 4096;
+            unsigned char *bh = st + 4 * kFwdChunk + (size_t)(c - 4 * nb) * kFwdChunk + h * 4096;
+            float2 fc[4][2];
+#pragma unroll
+            for (int bb = 0; bb < 4; ++bb)
+#pragma unroll
+                for (int qq = 0; qq < 2; ++qq) {
+                    const float2 v = fm[bb][qq];
+                    fc[bb][qq] = part ? make_float2(v.y * sX, v.x * sX) : make_float2(v.x * sX, -v.y * sX);
+                }
+#pragma unroll
+            for (int bb = 0; bb < 4; ++bb) {
+#pragma unroll
+                for (int a = 0; a < 8; ++a) {
+                    const float v0 = fmaf(e[a][0].x, fc[bb][0].x, e[a][0].y * fc[bb][0].y);
+                    const float v1 = fmaf(e[a][1].x, fc[bb][1].x, e[a][1].y * fc[bb][1].y);
+                    const uint32_t off = xo[a] + bb * 1024;
+                    uint32_t hi, lo;
+                    if (inA) {
+                        split2<BF16>(v0, v1, hi, lo);
+                        *reinterpret_cast<uint32_t *>(ah + off) = hi;
+                        *reinterpret_cast<uint32_t *>(ah + 2 * kFwdChunk + off) = lo;
+                    }
+                    if (inB) {
+                        const float wi = wr[bb][a] * sW;
+                        split2<BF16>(v0 * wi, v1 * wi, hi, lo);
+                        *reinterpret_cast<uint32_t *>(bh + off) = hi;
+                        *reinterpret_cast<uint32_t *>(bh + 4 * kFwdChunk + off) = lo;
+                    }
+                }
+            }
         };
         if (mine > 0 && my > 0) load(0, warp);
         for (int t = 0; t < mine; ++t) {
@@ -690,57 +740,15 @@ __device__ int wide_forward(const JobDev &J, unsigned char *dyn, uint64_t *bars,
             for (int q = 0; q < my; ++q) {
                 const int task = warp + 8 * q;
                 const int ci = task >> 1, h = task & 1, c = chunk[ci];
-                const int f = c * 64 + 2 * lane, part = f >= Kp;
-                float2 ec[8][2], fc[4][2];
-#pragma unroll
-                for (int a = 0; a < 8; ++a) {
-                    ec[a][0] = e[a][0];
-                    ec[a][1] = e[a][1];
-                }
-#pragma unroll
-                for (int bb = 0; bb < 4; ++bb) {
-                    fc[bb][0] = fm[bb][0];
-                    fc[bb][1] = fm[bb][1];
-                }
-                const float wc = wl;
-                // prefetch the next task of this warp
-                if (q + 1 < my) load(t, task + 8);
-                else if (t + 1 < mine) load(t + 1, warp);
-                // fold the part and sX into the E_m factors
-#pragma unroll
-                for (int bb = 0; bb < 4; ++bb)
-#pragma unroll
-                    for (int qq = 0; qq < 2; ++qq) {
-                        const float2 v = fc[bb][qq];
-                        fc[bb][qq] = part ? make_float2(v.y * sX, v.x * sX) : make_float2(v.x * sX, -v.y * sX);
-                    }
+                const int part = c * 64 + 2 * lane >= Kp;
                 const bool inA = c == 2 * m || c == 2 * m + 1;
                 const bool inB = c >= 4 * nb && 64 * c < 256 * nb + N;
-                unsigned char *ah = st + (size_t)(c - 2 * m) * kFwdChunk;
-                unsigned char *bh = st + 4 * kFwdChunk + (size_t)(c - 4 * nb) * kFwdChunk;
-#pragma unroll
-                for (int bb = 0; bb < 4; ++bb) {
-#pragma unroll
-                    for (int a = 0; a < 8; ++a) {
-                        const int r = 8 * (4 * h + bb) + a;
-                        const float wi = __shfl_sync(0xffffffffu, wc, bb * 8 + a);
-                        const float v0 = fmaf(ec[a][0].x, fc[bb][0].x, ec[a][0].y * fc[bb][0].y);
-                        const float v1 = fmaf(ec[a][1].x, fc[bb][1].x, ec[a][1].y * fc[bb][1].y);
-                        const uint32_t off = (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 +
-                                                        (((lane >> 2) ^ (r & 7)) << 4) + (lane & 3) * 4);
-                        uint32_t hi, lo;
-                        if (inA) {
-                            split2<BF16>(v0, v1, hi, lo);
-                            *reinterpret_cast<uint32_t *>(ah + off) = hi;
-                            *reinterpret_cast<uint32_t *>(ah + 2 * kFwdChunk + off) = lo;
-                        }
-                        if (inB) {
-                            split2<BF16>(v0 * wi, v1 * wi, hi, lo);
-                            *reinterpret_cast<uint32_t *>(bh + off) = hi;
-                            *reinterpret_cast<uint32_t *>(bh + 4 * kFwdChunk + off) = lo;
-                        }
-                    }
-                }
+                if (inA && inB) emit(st, c, h, part, std::true_type{}, std::true_type{});
+                else if (inA) emit(st, c, h, part, std::true_type{}, std::false_type{});
+                else emit(st, c, h, part, std::false_type{}, std::true_type{});
+                // next task of this warp (after the registers of this one are consumed)
+                if (q + 1 < my) load(t, task + 8);
+                else if (t + 1 < mine) load(t + 1, warp);
             }
             fence_async_smem();
             __syncwarp();
