@@ -530,9 +530,9 @@ __device__ void adjoint_list(const JobDev &J, const float2 *U, const int *pos, i
 
 // Full-image adjoint with generated steering vectors: epi(i, Re(a_i^H U a_i))
 // for every pixel, on one thread per pixel.
-template <int MODE, class Epi>
+template <int MODE, class Epi, class Pre>
 __device__ void adjoint_full(const JobDev &J, const float2 *U, float2 *A, TcWork &T, float *red,
-                             double *dbuf, Epi epi) {
+                             double *dbuf, Epi epi, Pre pre) {
     const int Q = J.Q;
     if constexpr (MODE == 0) {
         const int ntiles = (Q + kTile - 1) / kTile;
@@ -542,7 +542,10 @@ __device__ void adjoint_full(const JobDev &J, const float2 *U, float2 *A, TcWork
             fill_steer_adj(J, pix0, np, A);
             __syncthreads();
             adj_chunk(U, J.p, A, red);
-            if (threadIdx.x < np) epi(pix0 + threadIdx.x, red[threadIdx.x]);
+            if (threadIdx.x < np) {
+                pre(pix0 + threadIdx.x);
+                epi(pix0 + threadIdx.x, red[threadIdx.x]);
+            }
             __syncthreads();
         }
     } else {
@@ -561,8 +564,20 @@ __device__ void adjoint_full(const JobDev &J, const float2 *U, float2 *A, TcWork
                     if (i >= 0) epi(i, red[threadIdx.x] * inv);
                 }
                 __syncthreads();
+            },
+            [&](int t) {
+                if (threadIdx.x < kTcM) {
+                    const int i = tc_tile_pixel(t, threadIdx.x, J.n_l, J.n_m);
+                    if (i >= 0) pre(i);
+                }
             });
     }
+}
+
+template <int MODE, class Epi>
+__device__ void adjoint_full(const JobDev &J, const float2 *U, float2 *A, TcWork &T, float *red,
+                             double *dbuf, Epi epi) {
+    adjoint_full<MODE>(J, U, A, T, red, dbuf, epi, [](int) {});
 }
 
 // LSQR (Paige-Saunders) on the free set: min || b - M_F x ||, with
@@ -887,19 +902,29 @@ k_solve(JobDev *const *jobs, DevInfo *batch_info, double *const *sigma_out) {
                     const float *__restrict__ eps = J.eps;
                     const unsigned char *__restrict__ set = J.set;
                     float *__restrict__ grad = J.grad;
-                    adjoint_full<MODE>(J, Ug, A, T, S.red, S.dbuf, [&](int i, float val) {
-                        // lambda_L = g, lambda_U = -g (eq. etaL, eq. etaU); g and eps are FP32
-                        const float g = -scale[i] * val;
-                        grad[i] = g;
-                        const unsigned char st = set[i];
-                        if (st != IMG_SET_F) {
-                            const float lam = st == IMG_SET_U ? -g : g;
-                            if (lam < -eps[i] && (lam < bestf || (lam == bestf && i < bidx))) {
-                                bestf = lam;
-                                bidx = i;
+                    // this thread's pixel of the tile: its scale, threshold and set
+                    // are loaded before the tile's MMA is awaited
+                    float pscale = 0.f, peps = 0.f;
+                    unsigned char pset = 0;
+                    adjoint_full<MODE>(
+                        J, Ug, A, T, S.red, S.dbuf,
+                        [&](int i, float val) {
+                            // lambda_L = g, lambda_U = -g (eq. etaL, eq. etaU); g and eps are FP32
+                            const float g = -pscale * val;
+                            grad[i] = g;
+                            if (pset != IMG_SET_F) {
+                                const float lam = pset == IMG_SET_U ? -g : g;
+                                if (lam < -peps && (lam < bestf || (lam == bestf && i < bidx))) {
+                                    bestf = lam;
+                                    bidx = i;
+                                }
                             }
-                        }
-                    });
+                        },
+                        [&](int i) {
+                            pscale = scale[i];
+                            peps = eps[i];
+                            pset = set[i];
+                        });
                 }
                 best = bestf;
                 info.op_flops += flops_adj(p, Q);

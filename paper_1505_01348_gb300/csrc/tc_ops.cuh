@@ -118,6 +118,29 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Two 16-column tensor-memory loads, one wait.
+__device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float *a, float *b) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+        "[%32];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, "
+        "[%33];\n"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+          "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+          "=r"(r[30]), "=r"(r[31])
+        : "r"(ta), "r"(tb)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        a[i] = __uint_as_float(r[i]);
+        b[i] = __uint_as_float(r[16 + i]);
+    }
+}
+
 // ---------------------------------------------------------------- splitting
 // v = hi + lo in 16-bit parts; the 8 values of a 16-byte chunk at once.
 template <bool BF16>
@@ -143,6 +166,24 @@ __device__ __forceinline__ void split8(const float *v, uint4 &hi, uint4 &lo) {
     }
     hi = make_uint4(h[0], h[1], h[2], h[3]);
     lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// Two values -> hi and lo 16-bit pairs (packed conversions, round to nearest).
+template <bool BF16>
+__device__ __forceinline__ void split2(float v0, float v1, uint32_t &hi, uint32_t &lo) {
+    if (BF16) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+        hi = *reinterpret_cast<const uint32_t *>(&h);
+        lo = *reinterpret_cast<const uint32_t *>(&l);
+    } else {
+        const __half2 h = __floats2half2_rn(v0, v1);
+        const float2 hf = __half22float2(h);
+        const __half2 l = __floats2half2_rn(v0 - hf.x, v1 - hf.y);
+        hi = *reinterpret_cast<const uint32_t *>(&h);
+        lo = *reinterpret_cast<const uint32_t *>(&l);
+    }
 }
 
 // Byte offset of 16-byte chunk c (8 elements, covering K = 8c .. 8c+7) of
@@ -316,8 +357,10 @@ __device__ inline void tc_issue(const TcWork &T, int b, uint32_t idesc) {
 // t, epi(t, b) consumes accumulator b.  Generating tile t+1 and the epilogue
 // of tile t run while the tensor cores work on the other buffer.  The B tile
 // must be in place before the call.  All threads call this.
-template <class Gen, class Epi>
-__device__ inline void tc_run_tiles(TcWork &T, int ntiles, uint32_t idesc, Gen gen, Epi epi) {
+// pre(t) runs before tile t + 1 is generated, so loads that the epilogue of
+// tile t needs are in flight during the generation and the MMA.
+template <class Gen, class Epi, class Pre>
+__device__ inline void tc_run_tiles(TcWork &T, int ntiles, uint32_t idesc, Gen gen, Epi epi, Pre pre) {
     if (ntiles <= 0) return;
     gen(0, 0);
     fence_async_smem();
@@ -325,6 +368,7 @@ __device__ inline void tc_run_tiles(TcWork &T, int ntiles, uint32_t idesc, Gen g
     if (threadIdx.x == 0) tc_issue(T, 0, idesc);
     for (int t = 0; t < ntiles; ++t) {
         const int b = t & 1;
+        pre(t);
         if (t + 1 < ntiles) gen(t + 1, b ^ 1);
         fence_async_smem();
         if (!mbar_wait(&T.bar[b], T.phase[b])) T.timeouts++;
@@ -335,6 +379,12 @@ __device__ inline void tc_run_tiles(TcWork &T, int ntiles, uint32_t idesc, Gen g
         epi(t, b);
     }
 }
+
+template <class Gen, class Epi>
+__device__ inline void tc_run_tiles(TcWork &T, int ntiles, uint32_t idesc, Gen gen, Epi epi) {
+    tc_run_tiles(T, ntiles, idesc, gen, epi, [](int) {});
+}
+
 
 }  // namespace img
 
@@ -504,9 +554,14 @@ __device__ inline void tc_epilogue(const TcWork &T, int b, float *red) {
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
     const int nc8 = T.Kp / 8;
     float acc = 0.f;
-    for (int c0 = 0; c0 < T.Kp; c0 += 16) {
-        float d[16];
-        tmem_ld16(T.tmem + lane_base + (uint32_t)(b * 2 * T.Kp + half * T.Kp + c0), d);
+    for (int c00 = 0; c00 < T.Kp; c00 += 32) {
+        float dd[2][16];
+        const uint32_t ta = T.tmem + lane_base + (uint32_t)(b * 2 * T.Kp + half * T.Kp + c00);
+        tmem_ld16x2(ta, ta + 16, dd[0], dd[1]);
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+        const int c0 = c00 + 16 * g;
+        const float *d = dd[g];
 #pragma unroll
         for (int s8 = 0; s8 < 2; ++s8) {
             const uint32_t off = sw128_off(r, half * nc8 + c0 / 8 + s8, kTcM);
@@ -530,6 +585,7 @@ __device__ inline void tc_epilogue(const TcWork &T, int b, float *red) {
                 acc = fmaf(h0 + l0, d[s8 * 8 + 2 * q], acc);
                 acc = fmaf(h1 + l1, d[s8 * 8 + 2 * q + 1], acc);
             }
+        }
         }
     }
     red[half * kTcM + r] = acc;

@@ -80,47 +80,6 @@ __device__ __forceinline__ void tma_bulk_g2s(void *dst, const void *src, uint32_
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
-// Two 16-column tensor-memory loads, one wait.
-__device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float *a, float *b) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-        "[%32];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, "
-        "[%33];\n"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
-          "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
-          "=r"(r[30]), "=r"(r[31])
-        : "r"(ta), "r"(tb)
-        : "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        a[i] = __uint_as_float(r[i]);
-        b[i] = __uint_as_float(r[16 + i]);
-    }
-}
-
-// Two values -> hi and lo 16-bit pairs (packed conversions, round to nearest).
-template <bool BF16>
-__device__ __forceinline__ void split2(float v0, float v1, uint32_t &hi, uint32_t &lo) {
-    if (BF16) {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-        const float2 hf = __bfloat1622float2(h);
-        const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
-        hi = *reinterpret_cast<const uint32_t *>(&h);
-        lo = *reinterpret_cast<const uint32_t *>(&l);
-    } else {
-        const __half2 h = __floats2half2_rn(v0, v1);
-        const float2 hf = __half22float2(h);
-        const __half2 l = __floats2half2_rn(v0 - hf.x, v1 - hf.y);
-        hi = *reinterpret_cast<const uint32_t *>(&h);
-        lo = *reinterpret_cast<const uint32_t *>(&l);
-    }
-}
-
 // 8-byte asynchronous global -> shared copy (zero-filled when !valid; src
 // must still be a readable address).
 __device__ __forceinline__ void cp_async8(void *dst, const void *src, bool valid) {
