@@ -227,9 +227,10 @@ def run_ours(args, rank: int, world: int):
 
 
 # ---------------------------------------------------------------- serving
-def run_operators(args, cases=((128, 256), (256, 256), (256, 512)), reps: int = 20):
-    """Operator pair on wide arrays (64 < p <= 256) on full n x n grids
-    (256x256 as in the serving mix, and 512x512 at p = 256).
+def run_operators(args, cases=((64, 256), (128, 256), (256, 256), (256, 512)), reps: int = 20):
+    """Operator pair on full n x n grids: p = 64 (operands in shared memory:
+    k_psi_adj_tc, k_psi_partial_tc) and wide arrays 64 < p <= 256 (256x256 as
+    in the serving mix, and 512x512 at p = 256).
     Adjoint Psi^H (Eq. 16): the streamed tensor-core kernel; each call reduces
     max |U|, writes the chunked operand image from the complex128 U and runs
     the adjoint; calls are queued back to back on one stream and timed with
@@ -248,7 +249,7 @@ def run_operators(args, cases=((128, 256), (256, 256), (256, 512)), reps: int = 
     pk = measured_peaks()
     peak = float(pk.get("bf16_tflops") or 1900.0)
     out_d = {"grids": "n x n pixels per case (key p<p>_<n>)", "precision": args.precision,
-             "kernels": "k_psi_adj_wide (adjoint), k_fwd_wide (forward)",
+             "kernels": "p <= 64: k_psi_adj_tc, k_psi_partial_tc; 64 < p <= 256: k_psi_adj_wide, k_fwd_wide",
              "per_call": ("adjoint: max |U| reduction + operand image + adjoint (U read in place); forward: "
                           "FP32 weights + max |w| + Gram blocks + ordered partial sums into K"),
              "peak_tflops": peak,

@@ -202,8 +202,9 @@ img_status img_psi(img_ctx *ctx, const double *x, double *Kout, int on_device);
 
 /* Adjoint operator (Psi^H vect(U))_i = Re(a_i^H U a_i) (Sec. V-B):
  * U p x p Hermitian complex128 column-major -> out[0..Q) double.
- * Tensor-core arithmetic (IMG_PREC_F16X3 / BF16X3) up to p = 256; above
- * p = 64 the operand streams from global memory.
+ * Tensor-core arithmetic (IMG_PREC_F16X3 / BF16X3) up to p = 256, in the
+ * warp-specialised kernel that streams the operand from global memory; the
+ * forward (img_psi) likewise forms tensor-core Gram blocks.
  * img_psi and img_psi_adj also take on_device = 2: device pointers, work
  * queued on the context's stream and the call returns without waiting
  * (the caller orders or synchronises with that stream). */

@@ -108,9 +108,9 @@ size_t carve(img_ctx *c, char *base) {
     J.ev = cv.take<int>(J.ev_cap);
     J.evv = cv.take<float>(J.ev_cap);
     J.ev_count = cv.take<int>(1);
-    J.Bimg = (p > img::kMaxTcP && p <= img::kMaxWideP) ? cv.take<unsigned char>(2 * img::wide_B_bytes(p)) : nullptr;
+    J.Bimg = p <= img::kMaxWideP ? cv.take<unsigned char>(2 * img::wide_B_bytes(p)) : nullptr;
     J.Bscale = cv.take<float>(2);
-    J.Bmax = (p > img::kMaxTcP && p <= img::kMaxWideP) ? cv.take<unsigned>(2) : nullptr;
+    J.Bmax = p <= img::kMaxWideP ? cv.take<unsigned>(2) : nullptr;
     J.info = cv.take<DevInfo>(1);
     J.flags = cv.take<int>(4);
     c->dj = cv.take<JobDev>(1);
@@ -129,8 +129,9 @@ int mode_of(const img_ctx *c) {
     return (c->prm.precision != IMG_PREC_FP32 && c->prm.p <= img::kMaxTcP) ? c->prm.precision : 0;
 }
 
-// Arithmetic of the stand-alone adjoint (dirty image, bounds, Psi^H): tensor
-// cores up to p = 256 (streamed operand above p = 64).
+// Arithmetic of the stand-alone operators (dirty image, bounds, Psi, Psi^H):
+// tensor cores up to p = 256.  Bounds stream their operand above p = 64;
+// img_psi / img_psi_adj use the pipelined streamed kernels at every p.
 int op_mode_of(const img_ctx *c) {
     return (c->prm.precision != IMG_PREC_FP32 && c->prm.p <= img::kMaxWideP) ? c->prm.precision : 0;
 }
@@ -479,7 +480,7 @@ img_status img_psi(img_ctx *c, const double *x, double *Kout, int on_device) {
         CK(cudaStreamSynchronize(c->stream));
     }
     const int om = op_mode_of(c);
-    if (om != 0 && p > img::kMaxTcP) {
+    if (om != 0) {
         // tensor-core Gram blocks; their partial sums need a scratch buffer
         if (!c->fwd_part) {
             int sms = 1;
@@ -501,7 +502,7 @@ img_status img_psi_adj(img_ctx *c, const double *U, double *out, int on_device) 
     if (!c || !U || !out) return IMG_EINVAL;
     const int Q = c->hj.Q, p = c->prm.p;
     const int om = op_mode_of(c);
-    if (om != 0 && p > img::kMaxTcP) {
+    if (om != 0) {
         // streamed tensor-core operator: its operand image is built from the
         // complex128 U directly (the caller's device buffer, or a staged copy)
         const double2 *Ud = reinterpret_cast<const double2 *>(U);

@@ -1335,7 +1335,7 @@ size_t psi_wide_part_floats(int sms) { return (size_t)sms * kTcM * 256 + (size_t
 
 cudaError_t launch_psi_wide(const JobDev *job_dev, unsigned *wbits, const float *wx, float *part, int Q, int p,
                             int n_l, int n_m, int mode, double2 *Kout, cudaStream_t st) {
-    if (p <= kMaxTcP || p > kMaxWideP || (mode != 1 && mode != 2)) return cudaErrorInvalidValue;
+    if (p < 1 || p > kMaxWideP || (mode != 1 && mode != 2)) return cudaErrorInvalidValue;
     FwdMap map{};
     map.np = fwd_pairs(p, map.m, map.nb);
     for (int a = 0; a < 4; ++a)
@@ -1400,7 +1400,7 @@ static cudaError_t launch_psi_adj_wide_t(const JobDev *job_dev, unsigned *bmax, 
 
 cudaError_t launch_psi_adj_wide(const JobDev *job_dev, unsigned *bmax, const void *U, bool u64, double *out,
                                 int Q, int p, int mode, cudaStream_t st) {
-    if (p <= kMaxTcP || p > kMaxWideP || (mode != 1 && mode != 2)) return cudaErrorInvalidValue;
+    if (p < 1 || p > kMaxWideP || (mode != 1 && mode != 2)) return cudaErrorInvalidValue;
     if (mode == 1) return launch_psi_adj_wide_t<1>(job_dev, bmax, U, u64, out, Q, p, st);
     return launch_psi_adj_wide_t<2>(job_dev, bmax, U, u64, out, Q, p, st);
 }
