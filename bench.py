@@ -228,9 +228,9 @@ def run_ours(args, rank: int, world: int):
 
 # ---------------------------------------------------------------- serving
 def run_operators(args, cases=((64, 256), (128, 256), (256, 256), (256, 512)), reps: int = 20):
-    """Operator pair on full n x n grids: p = 64 (operands in shared memory:
-    k_psi_adj_tc, k_psi_partial_tc) and wide arrays 64 < p <= 256 (256x256 as
-    in the serving mix, and 512x512 at p = 256).
+    """Operator pair img_psi_adj / img_psi on full n x n grids: p = 64, 128
+    and 256 on 256x256 (the serving mix's largest grid) and p = 256 on
+    512x512; both run the streamed, warp-specialised tensor-core kernels.
     Adjoint Psi^H (Eq. 16): the streamed tensor-core kernel; each call reduces
     max |U|, writes the chunked operand image from the complex128 U and runs
     the adjoint; calls are queued back to back on one stream and timed with
@@ -249,7 +249,7 @@ def run_operators(args, cases=((64, 256), (128, 256), (256, 256), (256, 512)), r
     pk = measured_peaks()
     peak = float(pk.get("bf16_tflops") or 1900.0)
     out_d = {"grids": "n x n pixels per case (key p<p>_<n>)", "precision": args.precision,
-             "kernels": "p <= 64: k_psi_adj_tc, k_psi_partial_tc; 64 < p <= 256: k_psi_adj_wide, k_fwd_wide",
+             "kernels": "k_psi_adj_wide (adjoint), k_fwd_wide (forward)",
              "per_call": ("adjoint: max |U| reduction + operand image + adjoint (U read in place); forward: "
                           "FP32 weights + max |w| + Gram blocks + ordered partial sums into K"),
              "peak_tflops": peak,
