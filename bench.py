@@ -305,6 +305,33 @@ def run_operators(args, cases=((64, 256), (128, 256), (256, 256), (256, 512)), r
     return out_d
 
 
+def run_ls_images(args, iters: int = 100):
+    """Unconstrained WLS image with every pixel free (img_ls_image): LSQR
+    on M = W Psi D^-1 over all Q pixels, a fixed 100 iterations (stopping
+    tolerances 0).  Each iteration applies the forward (4 p^2 Q useful flops)
+    and the adjoint (8 p^2 Q) to the whole image; wall time of the call,
+    including the factor and bounds it starts with."""
+    import paper_1505_01348_gb300 as G
+    import synth
+
+    prec = PRECISIONS[args.precision]
+    out = {"iterations": iters, "precision": args.precision, "cost": "pwls"}
+    for name, job in (("bench_128x128_p64", synth.mid()),
+                      ("p256_256x256", synth.custom(7256, 256, 256, 256, 20, 10_000, radius=50.0))):
+        im = G.Imager.from_job(job, precision=prec, lsqr_atol=0.0, lsqr_btol=0.0)
+        im.ls_image(maxit=5)                       # warm-up (allocations, kernels)
+        ts = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            _, info = im.ls_image(maxit=iters)
+            ts.append(time.perf_counter() - t0)
+        im.close()
+        t = min(ts)
+        out[name] = {"s_per_image": t, "images_s": 1.0 / t, "lsqr_iters": info.lsqr_iters,
+                     "useful_operator_tflops": info.op_flops / t / 1e12}
+    return out
+
+
 def run_serve(args, rate: float = 200.0, seconds: float = 10.0, distinct: int = 48):
     """Poisson arrivals of mixed jobs into the continuous-batching server;
     latencies are the server's submit-to-done times."""
@@ -468,7 +495,7 @@ def main():
         if rank == 0:
             import paper_1505_01348_gb300 as G
             G.load()
-            print(json.dumps({"operators": run_operators(args)}), flush=True)
+            print(json.dumps({"operators": run_operators(args), "ls_image": run_ls_images(args)}), flush=True)
         return
     if world > 1:
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
@@ -521,6 +548,8 @@ def main():
         }
         if not args.no_ops and world == 1:
             line["operators"] = run_operators(args)
+            if PRECISIONS[args.precision] != 0:
+                line["ls_image"] = run_ls_images(args)
         if not args.no_serve and world == 1:
             line["serve"] = run_serve(args)
         if not args.no_cpu and world == 1:

@@ -210,6 +210,21 @@ img_status img_psi(img_ctx *ctx, const double *x, double *Kout, int on_device);
  * (the caller orders or synchronises with that stream). */
 img_status img_psi_adj(img_ctx *ctx, const double *U, double *out, int on_device);
 
+/* Unconstrained LS / WLS image with every pixel free (Sec. III-B/C: the LS
+ * and WLS images; Sec. V-A: LSQR): min ||b - M x|| over all Q pixels with
+ * M = Psi, b = vect(R_hat) (IMG_COST_LS) or M = W Psi D^-1, b = W vect(R_hat)
+ * (IMG_COST_PWLS, W = conj(L^-1) kron L^-1), cold start x0 = 0, no bounds.
+ * The bidiagonalisation runs on the device (operators as in img_psi /
+ * img_psi_adj, FP64 scalar recurrences in a one-thread kernel); the
+ * Paige-Saunders stopping tests with the context's lsqr_atol / lsqr_btol are
+ * checked every 10 iterations.  maxit <= 0: 200 iterations at most.
+ * sigma[0..Q) receives the image (host or device per on_device); info (may
+ * be NULL): lsqr_iters, converged (1 when a stopping test held),
+ * lambda_min = final residual norm estimate, op_flops, t_end_ns = wall time.
+ * Work buffers are allocated on the first call and kept with the context.
+ * Errors: IMG_EINVAL (no covariance), IMG_ENOTPD, IMG_ECUDA. */
+img_status img_ls_image(img_ctx *ctx, int maxit, double *sigma, img_solve_info *info, int on_device);
+
 /* Factor R_hat, dirty images and bounds of several jobs in single launches
  * (the step img_solve_batch would otherwise run first).  Every context must
  * hold a covariance and use the same device; runs on ctxs[0]'s stream.

@@ -24,7 +24,7 @@ SET_L, SET_U, SET_F = 0, 1, 2
 EXPORTS = ("img_params_default", "img_create", "img_set_covariance", "img_dirty",
            "img_mvdr_bound", "img_solve", "img_get_sets", "img_get_gradient", "img_get_events",
            "img_psi",
-           "img_psi_adj", "img_prepare_batch", "img_solve_batch", "img_psi_noalloc",
+           "img_psi_adj", "img_ls_image", "img_prepare_batch", "img_solve_batch", "img_psi_noalloc",
            "img_server_params_default", "img_server_create", "img_server_reserve", "img_server_submit",
            "img_server_wait", "img_server_destroy", "img_destroy", "img_status_str")
 
@@ -96,6 +96,8 @@ def load(build_if_missing: bool = False) -> C.CDLL:
         getattr(lib, name).restype = i
     lib.img_solve.argtypes = [vp, dp, C.POINTER(SolveInfo), i]
     lib.img_solve.restype = i
+    lib.img_ls_image.argtypes = [vp, i, dp, C.POINTER(SolveInfo), i]
+    lib.img_ls_image.restype = i
     lib.img_get_sets.argtypes = [vp, dp]
     lib.img_get_sets.restype = i
     lib.img_get_gradient.argtypes = [vp, dp]
@@ -233,6 +235,15 @@ class Imager:
 
     def mvdr_bound(self, out=None):
         return self._qvec(self._lib.img_mvdr_bound, out, "img_mvdr_bound")
+
+    def ls_image(self, maxit=0, out=None):
+        """Unconstrained LS / WLS image, every pixel free (img_ls_image)."""
+        if out is None:
+            out = np.empty(self.Q, dtype=np.float64)
+        info = SolveInfo()
+        _check(self._lib.img_ls_image(self.h, int(maxit), _ptr(out), C.byref(info), 1 if _is_device(out) else 0),
+               "img_ls_image")
+        return out, info
 
     def solve(self, out=None, allow=(IMG_ENOTCONV,)):
         if out is None:

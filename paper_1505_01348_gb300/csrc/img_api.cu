@@ -1,5 +1,6 @@
 // Host side of the C ABI declared in include/img.h: validation, device
 // memory layout of a job, and the launch sequence of every call.
+#include <chrono>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -37,6 +38,7 @@ struct img_ctx {
     double2 *Z = nullptr;        // p*p complex128 staging
     double *outd = nullptr;      // Q doubles staging
     float *fwd_part = nullptr;   // partial Gram blocks of the wide forward (allocated on first use)
+    void *ls_mem = nullptr;      // full-image LSQR vectors (allocated on first use)
 };
 
 namespace {
@@ -525,6 +527,87 @@ img_status img_psi_adj(img_ctx *c, const double *U, double *out, int on_device) 
     return copy_out_double(c, c->outd, out, Q, 0);
 }
 
+img_status img_ls_image(img_ctx *c, int maxit, double *sigma, img_solve_info *info, int on_device) {
+    if (!c || !sigma || !c->has_cov) return IMG_EINVAL;
+    img_status st = prepare(c);
+    if (st != IMG_OK) return st;
+    const int Q = c->hj.Q, p = c->prm.p, pp = p * p;
+    const int mode = op_mode_of(c);
+    // vectors: u, Mv, T1, Uw (p^2 float2), Kd (p^2 double2), v, w, x, wx (Q
+    // floats), y and sigma staging (Q doubles), scalars
+    auto al = [](size_t n) { return (n + 255) / 256 * 256; };
+    const size_t need = 4 * al((size_t)pp * sizeof(float2)) + al((size_t)pp * sizeof(double2)) +
+                        4 * al((size_t)Q * sizeof(float)) + 2 * al((size_t)Q * sizeof(double)) +
+                        al(img::kLsScalars * sizeof(double));
+    if (!c->ls_mem) CK(cudaMalloc(&c->ls_mem, need));
+    if (mode != 0 && !c->fwd_part) {
+        int sms = 1;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+        CK(cudaMalloc(&c->fwd_part, img::psi_wide_part_floats(sms) * sizeof(float)));
+    }
+    char *m = static_cast<char *>(c->ls_mem);
+    auto take = [&](size_t n) {
+        char *r = m;
+        m += al(n);
+        return r;
+    };
+    img::LsBufs b;
+    b.u = reinterpret_cast<float2 *>(take((size_t)pp * sizeof(float2)));
+    b.Mv = reinterpret_cast<float2 *>(take((size_t)pp * sizeof(float2)));
+    b.T1 = reinterpret_cast<float2 *>(take((size_t)pp * sizeof(float2)));
+    b.Uw = reinterpret_cast<float2 *>(take((size_t)pp * sizeof(float2)));
+    b.Kd = reinterpret_cast<double2 *>(take((size_t)pp * sizeof(double2)));
+    b.v = reinterpret_cast<float *>(take((size_t)Q * sizeof(float)));
+    b.w = reinterpret_cast<float *>(take((size_t)Q * sizeof(float)));
+    b.x = reinterpret_cast<float *>(take((size_t)Q * sizeof(float)));
+    b.wx = reinterpret_cast<float *>(take((size_t)Q * sizeof(float)));
+    b.y = reinterpret_cast<double *>(take((size_t)Q * sizeof(double)));
+    double *sig = reinterpret_cast<double *>(take((size_t)Q * sizeof(double)));
+    b.sc = reinterpret_cast<double *>(take(img::kLsScalars * sizeof(double)));
+    const auto t0 = std::chrono::steady_clock::now();
+    CK(img::ls_begin(c->dj, c->hj, b, mode, c->stream));
+    const int lim = maxit > 0 ? maxit : 200;
+    const double atol = c->prm.lsqr_atol, btol = c->prm.lsqr_btol;
+    int it = 0, istop = 3;
+    double h[img::kLsScalars] = {};
+    for (it = 1; it <= lim; ++it) {
+        CK(img::ls_iterate(c->dj, c->hj, b, mode, c->fwd_part, c->part, c->nparts, c->stream));
+        if (it % 10 == 0 || it == lim) {
+            // Paige-Saunders stopping tests on the host, every 10 iterations
+            CK(img::ls_xnorm2(c->hj, b, b.sc + img::kLsXnorm2, c->stream));
+            CK(cudaMemcpyAsync(h, b.sc, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            const double anorm = std::sqrt(h[img::kLsAnorm2]), xnorm = std::sqrt(h[img::kLsXnorm2]);
+            if (h[img::kLsRnorm] <= btol * h[img::kLsBnorm] + atol * anorm * xnorm) {
+                istop = 1;
+                break;
+            }
+            if (h[img::kLsArnorm] <= atol * anorm * h[img::kLsRnorm]) {
+                istop = 2;
+                break;
+            }
+        }
+    }
+    if (it > lim) it = lim;
+    CK(img::ls_finish(c->hj, b, on_device ? sigma : sig, nullptr, c->stream));
+    if (!on_device) CK(cudaMemcpyAsync(sigma, sig, (size_t)Q * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info) {
+        std::memset(info, 0, sizeof(*info));
+        info->status = IMG_OK;
+        info->outer = 0;
+        info->lsqr_iters = it;
+        info->n_free = Q;
+        info->converged = istop < 3 ? 1 : 0;
+        info->lambda_min = h[img::kLsRnorm];
+        info->op_flops = (double)(it + 1) * 8.0 * pp * Q + (double)it * 4.0 * pp * Q;
+        info->t_begin_ns = 0.0;
+        info->t_end_ns = secs * 1e9;
+    }
+    return IMG_OK;
+}
+
 }  // extern "C"
 
 namespace {
@@ -680,6 +763,7 @@ void img_destroy(img_ctx *c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->dmem) cudaFree(c->dmem);
     if (c->fwd_part) cudaFree(c->fwd_part);
+    if (c->ls_mem) cudaFree(c->ls_mem);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }

@@ -104,6 +104,30 @@ cudaError_t launch_job(JobDev *const *jobs, int n, int max_p, int mode, DevInfo 
                        double *const *sigma_out, cudaStream_t st);
 cudaError_t launch_psi(const JobDev *job_dev, const float *wx, float2 *part, int nparts, int Q,
                        int p, int mode, double2 *Kout, cudaStream_t st);
+// Full-image LSQR (all pixels free): device vectors and FP64 scalars
+// (kLsScalars doubles, indexed by kLs*); Q floats v, w, x, wx,
+// Q doubles y; p x p complex u, Mv, T1, Uw (FP32) and Kd (FP64).
+constexpr int kLsScalars = 16;
+enum : int { kLsSsU = 0, kLsSsV, kLsAlpha, kLsBeta, kLsRhobar, kLsPhibar, kLsAnorm2, kLsT1, kLsT2, kLsIa,
+             kLsBnorm, kLsRnorm, kLsArnorm, kLsUs, kLsXnorm2, kLsCount };
+static_assert(kLsCount <= kLsScalars, "LSQR scalar block");
+struct LsBufs {
+    float2 *u, *Mv, *T1, *Uw;
+    double2 *Kd;
+    float *v, *w, *x, *wx;
+    double *y, *sc;
+};
+// u = b / ||b||, v = M^H u / alpha, w = v, x = 0 (eq. initbeta, eq. initu).
+cudaError_t ls_begin(const JobDev *jd, const JobDev &hj, LsBufs &b, int mode, cudaStream_t st);
+// One Golub-Kahan step (eq. lanczos) with the Paige-Saunders rotation and
+// the x, w updates.  mode 0: CUDA-core operators (part/nparts scratch);
+// 1/2: tensor-core operators (fwd_part scratch).
+cudaError_t ls_iterate(const JobDev *jd, const JobDev &hj, LsBufs &b, int mode, float *fwd_part, float2 *part,
+                       int nparts, cudaStream_t st);
+// sigma = scale o x (device, Q doubles); *xnorm2 (device) = ||x||^2 if given.
+cudaError_t ls_finish(const JobDev &hj, LsBufs &b, double *sigma, double *xnorm2, cudaStream_t st);
+cudaError_t ls_xnorm2(const JobDev &hj, LsBufs &b, double *out, cudaStream_t st);
+
 // Wide tensor-core forward K = Psi w (64 < p <= 256, mode 1 or 2): wbits is
 // a device word (cleared here), part a scratch of psi_wide_part_floats(SMs)
 // floats; Kout p x p complex128.

@@ -368,6 +368,168 @@ __global__ void k_fwd_assemble(int p, const double *Ub, FwdMap map, const unsign
     }
 }
 
+// ---------------------------------------------------------------- full-image LSQR
+// Unconstrained LS / WLS image with every pixel free: LSQR (Sec. V-A) on
+// M = Psi (CLS) or W Psi D^-1 (PWLS, W = conj(L^-1) kron L^-1), b = vect(R_hat)
+// or W vect(R_hat) = vect(I).  The bidiagonalisation runs as a stream of
+// kernels: the operators above, complex p x p products for the whitening,
+// one-CTA reductions in a fixed order, and a one-thread kernel for the FP64
+// scalar recurrences, whose results later kernels read from device memory.
+
+// out = sum of squares of n floats (complex: 2n floats), one CTA, fixed order.
+__global__ void k_sumsq(const float *x, int n, double *out) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc = fma((double)x[i], (double)x[i], acc);
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        *out = s;
+    }
+}
+
+// FP64 scalars (one thread).  phase 0: beta of b; 1: alpha of the first v;
+// 2: beta of an iteration; 3: alpha, rotation and update coefficients.
+__global__ void k_ls_scalar(double *sc, int phase) {
+    if (threadIdx.x != 0) return;
+    if (phase == 0) {
+        const double beta = sqrt(sc[kLsSsU]);
+        sc[kLsBeta] = beta;
+        sc[kLsBnorm] = beta;
+        sc[kLsUs] = beta > 0.0 ? 1.0 / beta : 0.0;
+    } else if (phase == 1) {
+        const double alpha = sqrt(sc[kLsSsV]);
+        sc[kLsAlpha] = alpha;
+        sc[kLsIa] = alpha > 0.0 ? 1.0 / alpha : 1.0;
+        sc[kLsPhibar] = sc[kLsBeta];
+        sc[kLsRhobar] = alpha;
+        sc[kLsAnorm2] = 0.0;
+        sc[kLsRnorm] = sc[kLsBeta];
+        sc[kLsArnorm] = alpha * sc[kLsBeta];
+    } else if (phase == 2) {
+        const double beta = sqrt(sc[kLsSsU]), alpha = sc[kLsAlpha];
+        sc[kLsBeta] = beta;
+        sc[kLsUs] = beta > 0.0 ? 1.0 / beta : 0.0;
+        sc[kLsAnorm2] += alpha * alpha + beta * beta;
+    } else {
+        const double alpha = sqrt(sc[kLsSsV]), beta = sc[kLsBeta];
+        const double rhobar = sc[kLsRhobar], phibar = sc[kLsPhibar];
+        const double rho = hypot(rhobar, beta);
+        const double c = rhobar / rho, s = beta / rho;
+        const double theta = s * alpha, phi = c * phibar;
+        sc[kLsAlpha] = alpha;
+        sc[kLsIa] = alpha > 0.0 ? 1.0 / alpha : 1.0;
+        sc[kLsRhobar] = -c * alpha;
+        sc[kLsPhibar] = s * phibar;
+        sc[kLsT1] = phi / rho;
+        sc[kLsT2] = -theta / rho;
+        sc[kLsRnorm] = s * phibar;
+        sc[kLsArnorm] = s * phibar * alpha * fabs(c);
+    }
+}
+
+// u = b: vect(R_hat) (CLS) or vect(I) (PWLS, W vect(R_hat) = vect(L^-1 R L^-H)).
+__global__ void k_ls_init_u(const float2 *R32, int p, int pwls, float2 *u) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p * p; e += gridDim.x * blockDim.x) {
+        const int j = e / p, i = e - j * p;
+        u[e] = pwls ? make_float2(i == j ? 1.f : 0.f, 0.f) : R32[e];
+    }
+}
+// u *= us (u = t / beta).
+__global__ void k_ls_scale_u(float2 *u, int pp, const double *sc) {
+    const float us = (float)sc[kLsUs];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < pp; e += gridDim.x * blockDim.x)
+        u[e] = make_float2(u[e].x * us, u[e].y * us);
+}
+// u = Mv - alpha u.
+__global__ void k_ls_u(float2 *u, const float2 *Mv, int pp, const double *sc) {
+    const float a = (float)sc[kLsAlpha];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < pp; e += gridDim.x * blockDim.x) {
+        const float2 m = Mv[e], o = u[e];
+        u[e] = make_float2(m.x - a * o.x, m.y - a * o.y);
+    }
+}
+// wx = scale o v (the forward's pixel weights, D^-1 v for PWLS).
+__global__ void k_ls_weights(const float *scale, const float *v, float *wx, int Q) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Q; i += gridDim.x * blockDim.x) wx[i] = scale[i] * v[i];
+}
+// v = scale o y - beta v (first = true: v = scale o y).
+__global__ void k_ls_v(float *v, const double *y, const float *scale, int Q, const double *sc, int first) {
+    const float b = first ? 0.f : (float)sc[kLsBeta];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Q; i += gridDim.x * blockDim.x)
+        v[i] = scale[i] * (float)y[i] - (first ? 0.f : b * v[i]);
+}
+// v /= alpha; first: w = v, x = 0; else x += t1 w, w = v + t2 w.
+__global__ void k_ls_xw(float *x, float *w, float *v, int Q, const double *sc, int first) {
+    const float ia = (float)sc[kLsIa], t1 = (float)sc[kLsT1], t2 = (float)sc[kLsT2];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Q; i += gridDim.x * blockDim.x) {
+        const float vi = v[i] * ia;
+        v[i] = vi;
+        if (first) {
+            w[i] = vi;
+            x[i] = 0.f;
+        } else {
+            const float wi = w[i];
+            x[i] += t1 * wi;
+            w[i] = vi + t2 * wi;
+        }
+    }
+}
+__global__ void k_ls_sigma(const float *x, const float *scale, double *sigma, int Q) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Q; i += gridDim.x * blockDim.x)
+        sigma[i] = (double)scale[i] * (double)x[i];
+}
+__global__ void k_d2c(const double2 *src, float2 *dst, int n) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
+        dst[e] = make_float2((float)src[e].x, (float)src[e].y);
+}
+
+// C = op(A) op(B), p x p complex FP32 column-major; op 0: as is, 1: conjugate
+// transpose.  32 x 32 output tiles, 256 threads (2 x 2 outputs each).
+__global__ void k_cgemm(int p, const float2 *A, int opA, const float2 *B, int opB, float2 *C) {
+    __shared__ float2 As[32][33], Bs[32][33];
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float2 acc[2][2] = {};
+    for (int k0 = 0; k0 < p; k0 += 32) {
+        for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+            const int r = e & 31, c = e >> 5;           // As[r][c] = op(A)[i0 + r, k0 + c]
+            const int i = i0 + r, k = k0 + c;
+            float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+            if (i < p && k < p) {
+                a = opA ? A[(size_t)i * p + k] : A[(size_t)k * p + i];
+                if (opA) a.y = -a.y;
+            }
+            As[r][c] = a;
+            const int kk = k0 + r, j = j0 + c;          // Bs[r][c] = op(B)[k0 + r, j0 + c]
+            if (kk < p && j < p) {
+                b = opB ? B[(size_t)kk * p + j] : B[(size_t)j * p + kk];
+                if (opB) b.y = -b.y;
+            }
+            Bs[r][c] = b;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < 32; ++kk) {
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b) cfma(acc[a][b], As[2 * ty + a][kk], Bs[kk][2 * tx + b]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int i = i0 + 2 * ty + a, j = j0 + 2 * tx + b;
+            if (i < p && j < p) C[(size_t)j * p + i] = acc[a][b];
+        }
+}
+
 // Bounds, preconditioner and thresholds (one CTA per job):
 //   C = N/(N-p) or 1; mvdr = C/h; D = h^2/C; std_MF = dirty/sqrt(N);
 //   std_MVDR = mvdr/sqrt(N-p-1); gamma = chosen image, optionally inflated;
@@ -1360,6 +1522,88 @@ cudaError_t launch_psi_wide(const JobDev *job_dev, unsigned *wbits, const float 
     const int nent = map.np * kTcM * 256;
     k_fwd_reduce<<<(nent + 63) / 64, 256, 0, st>>>(part, S, nent, Ub);
     k_fwd_assemble<<<(p * p + kThreads - 1) / kThreads, kThreads, 0, st>>>(p, Ub, map, wbits, Kout);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- full-image LSQR launchers
+static inline int ls_grid(int n) { return max(1, min(4 * num_sms(), (n + kThreads - 1) / kThreads)); }
+
+cudaError_t ls_forward(const JobDev *jd, const JobDev &hj, LsBufs &b, int mode, float *fwd_part, float2 *part,
+                       int nparts, cudaStream_t st) {
+    const int Q = hj.Q, p = hj.p, pp = p * p;
+    k_ls_weights<<<ls_grid(Q), kThreads, 0, st>>>(hj.scale, b.v, b.wx, Q);
+    cudaError_t e = mode != 0 ? launch_psi_wide(jd, hj.Bmax + 1, b.wx, fwd_part, Q, p, hj.n_l, hj.n_m, mode, b.Kd, st)
+                              : launch_psi(jd, b.wx, part, nparts, Q, p, 0, b.Kd, st);
+    if (e != cudaSuccess) return e;
+    k_d2c<<<ls_grid(pp), kThreads, 0, st>>>(b.Kd, b.Mv, pp);
+    if (hj.cost == IMG_COST_PWLS) {
+        // W vect(K) = vect(L^-1 K L^-H)
+        const dim3 g((p + 31) / 32, (p + 31) / 32);
+        k_cgemm<<<g, kThreads, 0, st>>>(p, b.Mv, 0, hj.Li32, 1, b.T1);
+        k_cgemm<<<g, kThreads, 0, st>>>(p, hj.Li32, 0, b.T1, 0, b.Mv);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t ls_adjoint(const JobDev *jd, const JobDev &hj, LsBufs &b, int mode, cudaStream_t st) {
+    const int Q = hj.Q, p = hj.p;
+    const float2 *U = b.u;
+    if (hj.cost == IMG_COST_PWLS) {
+        // W^H vect(u) = vect(L^-H u L^-1)
+        const dim3 g((p + 31) / 32, (p + 31) / 32);
+        k_cgemm<<<g, kThreads, 0, st>>>(p, b.u, 0, hj.Li32, 0, b.T1);
+        k_cgemm<<<g, kThreads, 0, st>>>(p, hj.Li32, 1, b.T1, 0, b.Uw);
+        U = b.Uw;
+    }
+    cudaError_t e = mode != 0 ? launch_psi_adj_wide(jd, hj.Bmax, U, false, b.y, Q, p, mode, st)
+                              : launch_psi_adj(jd, U, b.y, Q, p, 0, st);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t ls_begin(const JobDev *jd, const JobDev &hj, LsBufs &b, int mode, cudaStream_t st) {
+    const int Q = hj.Q, p = hj.p, pp = p * p;
+    k_ls_init_u<<<ls_grid(pp), kThreads, 0, st>>>(hj.R32, p, hj.cost == IMG_COST_PWLS, b.u);
+    k_sumsq<<<1, 1024, 0, st>>>(reinterpret_cast<const float *>(b.u), 2 * pp, b.sc + kLsSsU);
+    k_ls_scalar<<<1, 32, 0, st>>>(b.sc, 0);
+    k_ls_scale_u<<<ls_grid(pp), kThreads, 0, st>>>(b.u, pp, b.sc);
+    cudaError_t e = ls_adjoint(jd, hj, b, mode, st);
+    if (e != cudaSuccess) return e;
+    k_ls_v<<<ls_grid(Q), kThreads, 0, st>>>(b.v, b.y, hj.scale, Q, b.sc, 1);
+    k_sumsq<<<1, 1024, 0, st>>>(b.v, Q, b.sc + kLsSsV);
+    k_ls_scalar<<<1, 32, 0, st>>>(b.sc, 1);
+    k_ls_xw<<<ls_grid(Q), kThreads, 0, st>>>(b.x, b.w, b.v, Q, b.sc, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t ls_iterate(const JobDev *jd, const JobDev &hj, LsBufs &b, int mode, float *fwd_part, float2 *part,
+                       int nparts, cudaStream_t st) {
+    const int Q = hj.Q, pp = hj.p * hj.p;
+    // u <- M v - alpha u, beta = ||u||, u <- u / beta
+    cudaError_t e = ls_forward(jd, hj, b, mode, fwd_part, part, nparts, st);
+    if (e != cudaSuccess) return e;
+    k_ls_u<<<ls_grid(pp), kThreads, 0, st>>>(b.u, b.Mv, pp, b.sc);
+    k_sumsq<<<1, 1024, 0, st>>>(reinterpret_cast<const float *>(b.u), 2 * pp, b.sc + kLsSsU);
+    k_ls_scalar<<<1, 32, 0, st>>>(b.sc, 2);
+    k_ls_scale_u<<<ls_grid(pp), kThreads, 0, st>>>(b.u, pp, b.sc);
+    // v <- M^H u - beta v, alpha = ||v||, rotation, x and w updates
+    e = ls_adjoint(jd, hj, b, mode, st);
+    if (e != cudaSuccess) return e;
+    k_ls_v<<<ls_grid(Q), kThreads, 0, st>>>(b.v, b.y, hj.scale, Q, b.sc, 0);
+    k_sumsq<<<1, 1024, 0, st>>>(b.v, Q, b.sc + kLsSsV);
+    k_ls_scalar<<<1, 32, 0, st>>>(b.sc, 3);
+    k_ls_xw<<<ls_grid(Q), kThreads, 0, st>>>(b.x, b.w, b.v, Q, b.sc, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t ls_finish(const JobDev &hj, LsBufs &b, double *sigma, double *xnorm2, cudaStream_t st) {
+    k_ls_sigma<<<ls_grid(hj.Q), kThreads, 0, st>>>(b.x, hj.scale, sigma, hj.Q);
+    if (xnorm2) k_sumsq<<<1, 1024, 0, st>>>(b.x, hj.Q, xnorm2);
+    return cudaGetLastError();
+}
+
+cudaError_t ls_xnorm2(const JobDev &hj, LsBufs &b, double *out, cudaStream_t st) {
+    k_sumsq<<<1, 1024, 0, st>>>(b.x, hj.Q, out);
     return cudaGetLastError();
 }
 
