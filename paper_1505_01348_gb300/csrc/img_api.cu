@@ -39,6 +39,7 @@ struct img_ctx {
     double *outd = nullptr;      // Q doubles staging
     float *fwd_part = nullptr;   // partial Gram blocks of the wide forward (allocated on first use)
     void *ls_mem = nullptr;      // full-image LSQR vectors (allocated on first use)
+    cudaGraphExec_t ls_exec = nullptr;   // one LSQR iteration as a CUDA graph (own stream only)
 };
 
 namespace {
@@ -571,7 +572,27 @@ img_status img_ls_image(img_ctx *c, int maxit, double *sigma, img_solve_info *in
     int it = 0, istop = 3;
     double h[img::kLsScalars] = {};
     for (it = 1; it <= lim; ++it) {
-        CK(img::ls_iterate(c->dj, c->hj, b, mode, c->fwd_part, c->part, c->nparts, c->stream));
+        if (c->ls_exec) {
+            CK(cudaGraphLaunch(c->ls_exec, c->stream));
+        } else {
+            CK(img::ls_iterate(c->dj, c->hj, b, mode, c->fwd_part, c->part, c->nparts, c->stream));
+            if (c->own_stream) {
+                // the iteration is a fixed sequence of ~15 launches on buffers the
+                // context keeps: record it once as a graph and replay it (the
+                // first, direct iteration has set every kernel attribute)
+                cudaGraph_t g = nullptr;
+                if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                    const cudaError_t e1 =
+                        img::ls_iterate(c->dj, c->hj, b, mode, c->fwd_part, c->part, c->nparts, c->stream);
+                    const cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+                    if (e1 == cudaSuccess && e2 == cudaSuccess && g) {
+                        if (cudaGraphInstantiate(&c->ls_exec, g, 0) != cudaSuccess) c->ls_exec = nullptr;
+                    }
+                    if (g) cudaGraphDestroy(g);
+                }
+                cudaGetLastError();      // a failed capture leaves direct launches in place
+            }
+        }
         if (it % 10 == 0 || it == lim) {
             // Paige-Saunders stopping tests on the host, every 10 iterations
             CK(img::ls_xnorm2(c->hj, b, b.sc + img::kLsXnorm2, c->stream));
@@ -763,6 +784,7 @@ void img_destroy(img_ctx *c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->dmem) cudaFree(c->dmem);
     if (c->fwd_part) cudaFree(c->fwd_part);
+    if (c->ls_exec) cudaGraphExecDestroy(c->ls_exec);
     if (c->ls_mem) cudaFree(c->ls_mem);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
