@@ -210,6 +210,15 @@ img_status img_psi(img_ctx *ctx, const double *x, double *Kout, int on_device);
  * (the caller orders or synchronises with that stream). */
 img_status img_psi_adj(img_ctx *ctx, const double *U, double *out, int on_device);
 
+/* Failure-detection self-test of the bounded waits that every tensor-core
+ * kernel uses (not part of the paper): one CTA on the current device waits on
+ * an mbarrier that receives its arrival only when arrive != 0, gives up after
+ * `polls` polls (1 .. 2^26) and frees its tensor memory on the normal exit
+ * path.  Returns IMG_ETIMEOUT when the wait ran out, IMG_OK when it completed,
+ * IMG_EINVAL for polls outside the range, IMG_ECUDA on a CUDA error.  The
+ * device stays usable either way; no fault or trap is involved. */
+img_status img_check_wait(unsigned polls, int arrive);
+
 /* Unconstrained LS / WLS image with every pixel free (Sec. III-B/C: the LS
  * and WLS images; Sec. V-A: LSQR): min ||b - M x|| over all Q pixels with
  * M = Psi, b = vect(R_hat) (IMG_COST_LS) or M = W Psi D^-1, b = W vect(R_hat)

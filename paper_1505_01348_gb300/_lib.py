@@ -24,7 +24,7 @@ SET_L, SET_U, SET_F = 0, 1, 2
 EXPORTS = ("img_params_default", "img_create", "img_set_covariance", "img_dirty",
            "img_mvdr_bound", "img_solve", "img_get_sets", "img_get_gradient", "img_get_events",
            "img_psi",
-           "img_psi_adj", "img_ls_image", "img_prepare_batch", "img_solve_batch", "img_psi_noalloc",
+           "img_psi_adj", "img_ls_image", "img_check_wait", "img_prepare_batch", "img_solve_batch", "img_psi_noalloc",
            "img_server_params_default", "img_server_create", "img_server_reserve", "img_server_submit",
            "img_server_wait", "img_server_destroy", "img_destroy", "img_status_str")
 
@@ -98,6 +98,8 @@ def load(build_if_missing: bool = False) -> C.CDLL:
     lib.img_solve.restype = i
     lib.img_ls_image.argtypes = [vp, i, dp, C.POINTER(SolveInfo), i]
     lib.img_ls_image.restype = i
+    lib.img_check_wait.argtypes = [C.c_uint, i]
+    lib.img_check_wait.restype = i
     lib.img_get_sets.argtypes = [vp, dp]
     lib.img_get_sets.restype = i
     lib.img_get_gradient.argtypes = [vp, dp]
@@ -301,6 +303,11 @@ class Imager:
         out = np.empty(self.Q, dtype=np.float64)
         _check(self._lib.img_psi_adj(self.h, U.ctypes.data, out.ctypes.data, 0), "img_psi_adj")
         return out
+
+
+def check_wait(polls: int, arrive: bool) -> int:
+    """Bounded-wait self-test (img_check_wait); returns the status code."""
+    return load().img_check_wait(int(polls), 1 if arrive else 0)
 
 
 def psi_noalloc(p, n_l, n_m, ant_xyz, l, m, lam, x, Kout, stream=0):

@@ -528,6 +528,18 @@ img_status img_psi_adj(img_ctx *c, const double *U, double *out, int on_device) 
     return copy_out_double(c, c->outd, out, Q, 0);
 }
 
+img_status img_check_wait(unsigned polls, int arrive) {
+    if (polls == 0 || polls > (1u << 26)) return IMG_EINVAL;
+    int *d = nullptr;
+    CK(cudaMalloc(&d, sizeof(int)));
+    int h = -1;
+    cudaError_t e = img::launch_wait_selftest(polls, arrive ? 1 : 0, d, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return IMG_ECUDA;
+    return h == IMG_OK ? IMG_OK : IMG_ETIMEOUT;
+}
+
 img_status img_ls_image(img_ctx *c, int maxit, double *sigma, img_solve_info *info, int on_device) {
     if (!c || !sigma || !c->has_cov) return IMG_EINVAL;
     img_status st = prepare(c);

@@ -104,6 +104,9 @@ cudaError_t launch_job(JobDev *const *jobs, int n, int max_p, int mode, DevInfo 
                        double *const *sigma_out, cudaStream_t st);
 cudaError_t launch_psi(const JobDev *job_dev, const float *wx, float2 *part, int nparts, int Q,
                        int p, int mode, double2 *Kout, cudaStream_t st);
+// Bounded-wait self-test (one CTA; *status: IMG_OK or IMG_ETIMEOUT).
+cudaError_t launch_wait_selftest(unsigned polls, int arrive, int *status, cudaStream_t st);
+
 // Full-image LSQR (all pixels free): device vectors and FP64 scalars
 // (kLsScalars doubles, indexed by kLs*); Q floats v, w, x, wx,
 // Q doubles y; p x p complex u, Mv, T1, Uw (FP32) and Kd (FP64).

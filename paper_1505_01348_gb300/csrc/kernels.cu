@@ -530,6 +530,38 @@ __global__ void k_cgemm(int p, const float2 *A, int opA, const float2 *B, int op
         }
 }
 
+// ---------------------------------------------------------------- failure detection
+// Self-test of the bounded waits every tensor-core kernel uses: one CTA
+// allocates tensor memory, waits on an mbarrier that receives an arrival only
+// when `arrive` is set, gives up after `polls` polls, frees the tensor memory
+// on its normal exit path and reports through *status (IMG_OK or
+// IMG_ETIMEOUT).  No fault, trap or endless loop is involved.
+__global__ void k_wait_selftest(unsigned polls, int arrive, int *status) {
+    __shared__ uint64_t bar;
+    __shared__ uint32_t slot;
+    __shared__ int timed_out;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        timed_out = 0;
+    }
+    if (threadIdx.x < 32) tmem_alloc(&slot, 32);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (arrive && threadIdx.x == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar)) : "memory");
+    if (!mbar_wait(&bar, 0u, polls)) atomicOr(&timed_out, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) tmem_dealloc(slot, 32);
+    if (threadIdx.x == 0) *status = timed_out ? IMG_ETIMEOUT : IMG_OK;
+}
+
+cudaError_t launch_wait_selftest(unsigned polls, int arrive, int *status, cudaStream_t st) {
+    k_wait_selftest<<<1, 64, 0, st>>>(polls, arrive, status);
+    return cudaGetLastError();
+}
+
 // Bounds, preconditioner and thresholds (one CTA per job):
 //   C = N/(N-p) or 1; mvdr = C/h; D = h^2/C; std_MF = dirty/sqrt(N);
 //   std_MVDR = mvdr/sqrt(N-p-1); gamma = chosen image, optionally inflated;

@@ -38,10 +38,11 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
 }
 
 // Wait until the barrier's phase with the given parity completes.  Returns
-// false after kSpinLimit polls (the caller records a timeout and goes on).
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// false after `limit` polls (kSpinLimit by default; the caller records a
+// timeout and goes on).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned limit = kSpinLimit) {
     const uint32_t a = smem_u32(bar);
-    for (unsigned it = 0; it < kSpinLimit; ++it) {
+    for (unsigned it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
