@@ -332,6 +332,75 @@ def run_ls_images(args, iters: int = 100):
     return out
 
 
+def _steer64(ant, l, m, lam, il, im):
+    """FP64 steering vectors of pixels (il, im), unit norm, -j sign (the data
+    model's definition; host check values, no oracle code)."""
+    n = np.sqrt(np.maximum(0.0, 1.0 - l[il] ** 2 - m[im] ** 2))
+    dirs = np.stack([l[il], m[im], n])
+    return np.exp(-2j * np.pi * (ant @ dirs) / lam) / np.sqrt(ant.shape[0])
+
+
+def run_precision(args):
+    """Arithmetic sweep against FP64 (config 4's report on the tensor-core
+    range): operators on the first 256 antennas of the p = 288 clustered
+    array (sub-array covariance R_hat[:256, :256]) on the 256x256 grid,
+    relative L2 errors on 256 sampled pixels (dirty image, MVDR bound) and of
+    Psi x for a 128-pixel sparse x on every 4th grid line, each against FP64
+    sums evaluated here; and
+    the bench image (128x128, p = 64, PWLS) against the stored FP64 oracle
+    record, with its Table I passes and LSQR iterations.  p = 288 itself has
+    only the FP32 path (tensor-core operands up to p = 256)."""
+    import paper_1505_01348_gb300 as G
+    import synth
+
+    big = synth.large()
+    p = 256
+    ant, R = big.ant_xyz[:p], big.R[:p, :p]
+    rng = np.random.default_rng(11)
+    Q = big.n_l * big.n_m
+    idx = rng.choice(Q, 256, replace=False)
+    As = _steer64(ant, big.l, big.m, big.lam, idx % big.n_l, idx // big.n_l)
+    d_ref = np.real(np.einsum("ki,kl,li->i", As.conj(), R, As))
+    h_ref = np.real(np.einsum("ki,kl,li->i", As.conj(), np.linalg.inv(R), As))
+    # Psi x on every 4th grid line (64x64): the FP32 forward at p = 256 splits
+    # the pixels over few CTAs, so the full grid would take seconds there
+    ls_, ms_ = big.l[::4], big.m[::4]
+    Qs = ls_.shape[0] * ms_.shape[0]
+    xs_idx = rng.choice(Qs, 128, replace=False)
+    xs_val = rng.uniform(0.1, 2.0, 128)
+    Ax = _steer64(ant, ls_, ms_, big.lam, xs_idx % ls_.shape[0], xs_idx // ls_.shape[0])
+    K_ref = (Ax * xs_val[None, :]) @ Ax.conj().T
+    x = np.zeros(Qs)
+    x[xs_idx] = xs_val
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    gold = np.load(os.path.join(ROOT, "tests", "golden", "mid_pwls.npz"))
+    out = {"operators": f"p = {p} (sub-array of the p = 288 clustered array), 256x256 grid",
+           "image": "bench image 128x128, p = 64, PWLS, vs the stored FP64 oracle record",
+           "oracle_outer_passes": int(gold["outer"]), "oracle_lsqr_iters": int(gold["lsqr_iters"])}
+    for name, prec in sorted(PRECISIONS.items(), key=lambda kv: kv[1]):
+        im = G.Imager(ant, big.l, big.m, big.lam, precision=prec)
+        im.set_covariance(R, big.N)
+        d, mv = im.dirty(), im.mvdr_bound()
+        im.close()
+        im = G.Imager(ant, ls_, ms_, big.lam, precision=prec)
+        im.set_covariance(R, big.N)
+        K = im.psi(x)
+        im.close()
+        imb = G.Imager(gold["ant_xyz"], gold["l"], gold["m"], float(gold["lam"]), cost=int(gold["cost"]),
+                       kappa=float(gold["kappa"]), eps_floor=float(gold["eps_floor"]),
+                       feas_tol=float(gold["feas_tol"]), precision=prec)
+        imb.set_covariance(gold["R"], int(gold["N"]))
+        t0 = time.perf_counter()
+        sigma, info = imb.solve()
+        ts = time.perf_counter() - t0
+        imb.close()
+        out[name] = {"dirty_rel": rel(d[idx], d_ref), "mvdr_rel": rel(mv[idx], 1.0 / h_ref),
+                     "psi_rel": rel(K, K_ref), "image_rel": rel(sigma, gold["sigma"]),
+                     "outer_passes": int(info.outer), "lsqr_iters": int(info.lsqr_iters),
+                     "solve_s": ts}
+    return out
+
+
 def run_serve(args, rate: float = 200.0, seconds: float = 10.0, distinct: int = 48):
     """Poisson arrivals of mixed jobs into the continuous-batching server;
     latencies are the server's submit-to-done times."""
@@ -480,7 +549,9 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-ops", action="store_true")
     ap.add_argument("--ops-only", action="store_true",
-                    help="only the wide-array adjoint measurement (one JSON line)")
+                    help="only the operator and full-image LS measurements (one JSON line)")
+    ap.add_argument("--precision-only", action="store_true",
+                    help="only the arithmetic sweep against FP64 (one JSON line)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -491,6 +562,12 @@ def main():
             run_reference(args)
         return
     import torch
+    if args.precision_only:
+        if rank == 0:
+            import paper_1505_01348_gb300 as G
+            G.load()
+            print(json.dumps({"precision_sweep": run_precision(args)}), flush=True)
+        return
     if args.ops_only:
         if rank == 0:
             import paper_1505_01348_gb300 as G
@@ -550,6 +627,7 @@ def main():
             line["operators"] = run_operators(args)
             if PRECISIONS[args.precision] != 0:
                 line["ls_image"] = run_ls_images(args)
+            line["precision_sweep"] = run_precision(args)
         if not args.no_serve and world == 1:
             line["serve"] = run_serve(args)
         if not args.no_cpu and world == 1:
