@@ -8,6 +8,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/img.h"
 #include "img_internal.cuh"
 #include "tc_wide.cuh"
@@ -53,6 +55,13 @@ img_status cuda_status(cudaError_t e) { return e == cudaSuccess ? IMG_OK : IMG_E
         cudaError_t _e = (x);                        \
         if (_e != cudaSuccess) return IMG_ECUDA;     \
     } while (0)
+
+// NVTX range over one API call (a no-op unless a profiler is attached), so
+// traces show set_covariance / factor+bounds / solve / operators per call.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 
 struct Carver {
     char *base;
@@ -149,6 +158,7 @@ img_status sync(img_ctx *c) { return cuda_status(cudaStreamSynchronize(c->stream
 
 // Factor, dirty image, bounds (once per covariance).
 img_status prepare(img_ctx *c) {
+    const Range range_("img.prepare");
     if (!c->has_cov) return IMG_EINVAL;
     if (c->prepared) return (img_status)c->prep_status;
     CK(img::launch_factor(c->djp, 1, c->stream));
@@ -366,6 +376,7 @@ img_status img_create(const img_params *prm, img_ctx **out) {
 }
 
 img_status img_set_covariance(img_ctx *c, const void *R, int dtype, long long N, int on_device) {
+    const Range range_("img.set_covariance");
     if (!c || !R) return IMG_EINVAL;
     if (dtype != IMG_C64 && dtype != IMG_C128) return IMG_EINVAL;
     const int p = c->prm.p;
@@ -415,6 +426,7 @@ img_status img_set_covariance(img_ctx *c, const void *R, int dtype, long long N,
 }
 
 img_status img_dirty(img_ctx *c, double *out, int on_device) {
+    const Range range_("img.dirty");
     if (!c || !out) return IMG_EINVAL;
     img_status st = prepare(c);
     if (st != IMG_OK) return st;
@@ -422,6 +434,7 @@ img_status img_dirty(img_ctx *c, double *out, int on_device) {
 }
 
 img_status img_mvdr_bound(img_ctx *c, double *out, int on_device) {
+    const Range range_("img.mvdr_bound");
     if (!c || !out) return IMG_EINVAL;
     img_status st = prepare(c);
     if (st != IMG_OK) return st;
@@ -429,6 +442,7 @@ img_status img_mvdr_bound(img_ctx *c, double *out, int on_device) {
 }
 
 img_status img_solve(img_ctx *c, double *sigma, img_solve_info *info, int on_device) {
+    const Range range_("img.solve");
     if (!c || !sigma) return IMG_EINVAL;
     img_status st = prepare(c);
     if (st != IMG_OK) return st;
@@ -472,6 +486,7 @@ img_status img_get_events(img_ctx *c, int *events, double *values, int capacity,
 }
 
 img_status img_psi(img_ctx *c, const double *x, double *Kout, int on_device) {
+    const Range range_("img.psi");
     if (!c || !x || !Kout) return IMG_EINVAL;
     const int Q = c->hj.Q, p = c->prm.p;
     if (on_device) {
@@ -502,6 +517,7 @@ img_status img_psi(img_ctx *c, const double *x, double *Kout, int on_device) {
 }
 
 img_status img_psi_adj(img_ctx *c, const double *U, double *out, int on_device) {
+    const Range range_("img.psi_adj");
     if (!c || !U || !out) return IMG_EINVAL;
     const int Q = c->hj.Q, p = c->prm.p;
     const int om = op_mode_of(c);
@@ -541,6 +557,7 @@ img_status img_check_wait(unsigned polls, int arrive) {
 }
 
 img_status img_ls_image(img_ctx *c, int maxit, double *sigma, img_solve_info *info, int on_device) {
+    const Range range_("img.ls_image");
     if (!c || !sigma || !c->has_cov) return IMG_EINVAL;
     img_status st = prepare(c);
     if (st != IMG_OK) return st;
@@ -707,6 +724,7 @@ img_status launch_prepare(const Groups &g, cudaStream_t s, int *status_out) {
 extern "C" {
 
 img_status img_prepare_batch(img_ctx *const *ctxs, int n) {
+    const Range range_("img.prepare_batch");
     img_status st = check_batch(ctxs, n);
     if (st != IMG_OK) return st;
     std::lock_guard<std::mutex> lock(g_ws.mu);
@@ -737,6 +755,7 @@ img_status img_prepare_batch(img_ctx *const *ctxs, int n) {
 
 img_status img_solve_batch(img_ctx *const *ctxs, int n, double *const *sigma, img_solve_info *infos,
                            int on_device) {
+    const Range range_("img.solve_batch");
     img_status st = check_batch(ctxs, n);
     if (st != IMG_OK) return st;
     if (!sigma) return IMG_EINVAL;

@@ -38,3 +38,29 @@ def test_device_usable_after_timeouts(G):
     im.close()
     ref = np.real(np.einsum("ki,kl,li->i", A.conj(), job.R, A))
     assert np.linalg.norm(d - ref) <= 1e-5 * np.linalg.norm(ref)
+
+
+def test_host_side_injections(G):
+    """Corrupted inputs are rejected before any launch; iteration caps stop
+    the solve with IMG_ENOTCONV and a valid partial image."""
+    job = synth.custom(5, 12, 10, 10, 3, 800, radius=4.0)
+    im = G.Imager(job.ant_xyz, job.l, job.m)
+    bad = job.R.copy()
+    bad[2, 3] = np.nan
+    bad[3, 2] = np.nan
+    with pytest.raises(G.ImgError) as e:
+        im.set_covariance(bad, job.N)
+    assert e.value.code == G.IMG_EINVAL
+    im.close()
+    for prec in (0, 1):
+        im = G.Imager.from_job(job, precision=prec, max_outer=1)
+        sigma, info = im.solve()
+        assert info.status == G.IMG_ENOTCONV and info.converged == 0
+        assert info.outer <= 1
+        assert np.all(np.isfinite(sigma)) and np.all(sigma >= 0)
+        assert np.all(sigma <= im.mvdr_bound() * (1 + 1e-5))
+        im.close()
+        im = G.Imager.from_job(job, precision=prec, lsqr_maxit=1)
+        sigma, info = im.solve()          # may or may not converge; must stay valid
+        assert np.all(np.isfinite(sigma)) and np.all(sigma >= 0)
+        im.close()
