@@ -1,4 +1,4 @@
-"""The oracle's decision-log replay (used to judge path-dependent GPU runs)
+"""The oracle's decision-log replay (used to check path-dependent GPU runs)
 accepts the oracle's own path and rejects a planted wrong decision."""
 import numpy as np
 
