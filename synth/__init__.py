@@ -24,6 +24,8 @@ which are not available):
 * ``large``  p=288 in 6 clusters of 48 within radius 200, 256x256 grid,
   50 point sources plus 3 Gaussian blobs (FWHM U[4,10] px).
 * ``serve``  p in {32,64,128,256}, n in {64,128,256}, 5-50 sources.
+* ``snapshots_*``  K snapshots of one sky with the array turned by dtheta
+  between snapshots (Earth rotation stand-in), independent noise per snapshot.
 """
 from __future__ import annotations
 
@@ -264,3 +266,114 @@ def serve_job_tc(j: int, seed: int = 6000, N: int = 10_000) -> Job:
     sky[_distinct_pixels(n * n, n_src, sk)] = sk.lognormal(0.0, 1.0, n_src)
     noise_var = float(sky.sum()) / p
     return _finish("serve_tc", seed + j, ant, l, m.copy(), 1.0, sky, noise_var, N, {"job": j})
+
+
+# ---------------------------------------------------------------- K > 1 snapshots
+@dataclass
+class SnapshotJob:
+    """One imaging job observed over K snapshots (Sec. II data model): the
+    sky is fixed, the array turns with the Earth between snapshots, and each
+    snapshot k has its own sample covariance R_k from N samples."""
+
+    name: str
+    seed: int
+    ant_xyz: np.ndarray          # (K, p, 3) positions per snapshot, sky-fixed frame
+    l: np.ndarray
+    m: np.ndarray
+    lam: float
+    R: np.ndarray                # (K, p, p) complex128 sample covariances
+    N: int
+    sigma_true: np.ndarray
+    noise_var: float
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def K(self) -> int:
+        return self.ant_xyz.shape[0]
+
+    @property
+    def p(self) -> int:
+        return self.ant_xyz.shape[1]
+
+    @property
+    def n_l(self) -> int:
+        return self.l.shape[0]
+
+    @property
+    def n_m(self) -> int:
+        return self.m.shape[0]
+
+    @property
+    def Q(self) -> int:
+        return self.n_l * self.n_m
+
+
+def rotate_layout(ant: np.ndarray, theta: float) -> np.ndarray:
+    """Turn an array about its local vertical by theta radians.  For an array
+    at a pole imaging the zenith region this is the apparent motion of the
+    array against the sky between snapshots."""
+    c, s = math.cos(theta), math.sin(theta)
+    out = ant.copy()
+    out[:, 0] = c * ant[:, 0] - s * ant[:, 1]
+    out[:, 1] = s * ant[:, 0] + c * ant[:, 1]
+    return out
+
+
+def _finish_snapshots(name, seed, ant0, K, dtheta, l, m, lam, sky, noise_var, N,
+                      meta=None) -> SnapshotJob:
+    ants = np.stack([rotate_layout(ant0, k * dtheta) for k in range(K)], axis=0)
+    Rs = np.stack([sample_covariance(ants[k], l, m, lam, sky, noise_var, N,
+                                     np.random.default_rng([int(seed), _NOISE, k]))
+                   for k in range(K)], axis=0)
+    return SnapshotJob(name=name, seed=seed, ant_xyz=ants, l=l, m=m, lam=lam, R=Rs, N=N,
+                       sigma_true=sky, noise_var=noise_var,
+                       meta=dict(meta or {}, dtheta=dtheta))
+
+
+def snapshots_custom(seed: int, p: int, n_l: int, n_m: int, n_src: int, N: int, K: int,
+                     dtheta: float = 0.2, radius: float = 10.0, snr_db: float = 0.0,
+                     half_width: float = 0.5) -> SnapshotJob:
+    """Small K-snapshot jobs for tests: disk array, on-grid point sources with
+    powers U[1, 10], noise set by the per-antenna SNR, the array turned by
+    dtheta radians from one snapshot to the next."""
+    ant = disk_layout(p, radius, _rng(seed, _ARRAY))
+    l = grid(n_l, half_width)
+    m = grid(n_m, half_width)
+    rs = _rng(seed, _SKY)
+    Q = n_l * n_m
+    sky = np.zeros(Q)
+    k = min(n_src, Q)
+    if k:
+        sky[_distinct_pixels(Q, k, rs)] = rs.uniform(1.0, 10.0, k)
+    noise_var = max(float(sky.sum()) / p * 10 ** (-snr_db / 10.0), 1e-3)
+    return _finish_snapshots("snapshots_custom", seed, ant, K, dtheta, l, m, 1.0, sky,
+                             noise_var, N)
+
+
+def snapshots_extended(seed: int = 7000, p: int = 100, n: int = 64, K: int = 2,
+                       N: int = 10_000, dtheta: float = 0.05) -> SnapshotJob:
+    """Stand-in for the extended-source simulation of Sec. VI: p = 100
+    antennas at random in a disk, K = 2 snapshots, one strong point source and
+    two extended structures of seven Gaussians each (one at the centre, six on
+    a hexagon around it), background noise 10 dB below the extended sources.
+    The paper's two snapshots are one second apart; dtheta is larger so that
+    the two snapshots see visibly different arrays."""
+    ant = disk_layout(p, 25.0, _rng(seed, _ARRAY))
+    l = m = grid(n)
+    rs = _rng(seed, _SKY)
+    Q = n * n
+    sky = np.zeros(Q)
+    sky[int(rs.integers(Q))] = 100.0
+    ext_peak = 1.0
+    for _ in range(2):
+        cl = int(rs.integers(n // 4, 3 * n // 4))
+        cm = int(rs.integers(n // 4, 3 * n // 4))
+        hexr = max(2, n // 16)
+        pts = [(cl, cm)] + [(int(round(cl + hexr * math.cos(t))), int(round(cm + hexr * math.sin(t))))
+                            for t in np.arange(6) * (math.pi / 3.0)]
+        for il, im in pts:
+            if 0 <= il < n and 0 <= im < n:
+                gaussian_blob(sky, n, n, il + n * im, 2.0, ext_peak)
+    noise_var = ext_peak * 10 ** (-1.0)
+    return _finish_snapshots("snapshots_extended", seed, ant, K, dtheta, l, m.copy(), 1.0,
+                             sky, noise_var, N)
