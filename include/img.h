@@ -234,6 +234,28 @@ img_status img_check_wait(unsigned polls, int arrive);
  * Errors: IMG_EINVAL (no covariance), IMG_ENOTPD, IMG_ECUDA. */
 img_status img_ls_image(img_ctx *ctx, int maxit, double *sigma, img_solve_info *info, int on_device);
 
+/* Dirty images over K > 1 snapshots (Sec. II: one sky seen by an array that
+ * turns with the Earth, one sample covariance R_hat_k per snapshot).  Each
+ * snapshot is a context of its own: snap[k] holds snapshot k's antenna
+ * positions and covariance.  With d_{i,k} = a_{i,k}^H R_hat_k a_{i,k} and
+ * h_{i,k} = a_{i,k}^H R_hat_k^{-1} a_{i,k} (each context's own dirty image and
+ * MVDR denominator), out[0..Q) receives
+ *   IMG_SNAP_MF    (1/K) sum_k d_{i,k}               MF dirty image, Sec. III-C
+ *   IMG_SNAP_MVDR  C K / sum_k h_{i,k}               unbiased MVDR, Sec. III-D, eq. C
+ *   IMG_SNAP_ASSC  C / max_k h_{i,k}                 ASSC bound, eq. ASSC0
+ * with C = N/(N-p) when bias_c is set, else 1; no inflation is applied.
+ * Sums run in snapshot order in FP64 over the contexts' FP32 per-pixel
+ * values, so K = 1 reproduces img_dirty and (uninflated) img_mvdr_bound bit
+ * for bit.  1 <= K <= IMG_MAX_SNAPSHOTS.  Every context must hold a
+ * covariance, use the same device, and agree on p, the grid (n_l, n_m, l,
+ * m), lambda, N and bias_c; otherwise IMG_EINVAL.  Each context's factor and
+ * bounds are computed if needed (IMG_ENOTPD if one fails); the combination
+ * runs on snap[0]'s stream and the call returns after it finished.  out is
+ * host or device memory per on_device. */
+enum { IMG_SNAP_MF = 0, IMG_SNAP_MVDR = 1, IMG_SNAP_ASSC = 2 };
+#define IMG_MAX_SNAPSHOTS 32
+img_status img_snapshot_image(img_ctx *const *snap, int K, int kind, double *out, int on_device);
+
 /* Factor R_hat, dirty images and bounds of several jobs in single launches
  * (the step img_solve_batch would otherwise run first).  Every context must
  * hold a covariance and use the same device; runs on ctxs[0]'s stream.

@@ -544,6 +544,38 @@ img_status img_psi_adj(img_ctx *c, const double *U, double *out, int on_device) 
     return copy_out_double(c, c->outd, out, Q, 0);
 }
 
+img_status img_snapshot_image(img_ctx *const *snap, int K, int kind, double *out, int on_device) {
+    const Range range_("img.snapshot_image");
+    if (!snap || !out || K < 1 || K > IMG_MAX_SNAPSHOTS) return IMG_EINVAL;
+    if (kind != IMG_SNAP_MF && kind != IMG_SNAP_MVDR && kind != IMG_SNAP_ASSC) return IMG_EINVAL;
+    for (int k = 0; k < K; ++k)
+        if (!snap[k] || !snap[k]->has_cov) return IMG_EINVAL;
+    img_ctx *c0 = snap[0];
+    for (int k = 1; k < K; ++k) {
+        const img_ctx *c = snap[k];
+        if (c->device != c0->device || c->prm.p != c0->prm.p || c->prm.n_l != c0->prm.n_l ||
+            c->prm.n_m != c0->prm.n_m || c->prm.lambda != c0->prm.lambda ||
+            c->prm.bias_c != c0->prm.bias_c || c->hj.N != c0->hj.N || c->l != c0->l || c->m != c0->m)
+            return IMG_EINVAL;
+    }
+    for (int k = 0; k < K; ++k) {
+        const img_status st = prepare(snap[k]);     // synchronises snapshot k's stream
+        if (st != IMG_OK) return st;
+    }
+    img::SnapPtrs sp{};
+    for (int k = 0; k < K; ++k) {
+        sp.d[k] = snap[k]->hj.dirty;
+        sp.h[k] = snap[k]->hj.h;
+    }
+    const long long N = c0->hj.N;
+    const int p = c0->prm.p;
+    const double C = c0->prm.bias_c ? (double)N / (double)(N - p) : 1.0;
+    const int Q = c0->hj.Q;
+    CK(img::launch_snapshot_image(sp, K, Q, kind, C, on_device ? out : c0->outd, c0->stream));
+    if (on_device) return sync(c0);
+    return copy_out_double(c0, c0->outd, out, Q, 0);
+}
+
 img_status img_check_wait(unsigned polls, int arrive) {
     if (polls == 0 || polls > (1u << 26)) return IMG_EINVAL;
     int *d = nullptr;

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/img.h"
+
 namespace img {
 
 constexpr int kThreads = 256;      // threads per CTA in every kernel
@@ -148,6 +150,13 @@ cudaError_t launch_z2c(const double2 *src, float2 *dst, int n, cudaStream_t st);
 cudaError_t launch_c2z(const float2 *src, double2 *dst, int n, cudaStream_t st);
 cudaError_t launch_d2f(const double *src, float *dst, int n, cudaStream_t st);
 cudaError_t launch_to_double(const float *src, double *dst, int n, cudaStream_t st);
+// Per-snapshot arrays for the K-snapshot dirty images (passed by value).
+struct SnapPtrs {
+    const float *d[IMG_MAX_SNAPSHOTS];   // MF dirty image of snapshot k
+    const float *h[IMG_MAX_SNAPSHOTS];   // a^H R_k^-1 a of snapshot k
+};
+cudaError_t launch_snapshot_image(const SnapPtrs &sp, int K, int Q, int kind, double C, double *out,
+                                  cudaStream_t st);
 
 size_t solve_smem_bytes(int p, int mode);
 constexpr int kMaxTcP = 64;   // tensor-core solver: 2p x 2p operand tiles in shared memory

@@ -1709,6 +1709,32 @@ cudaError_t launch_d2f(const double *src, float *dst, int n, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Dirty images over K snapshots from each snapshot's MF image d_k and MVDR
+// denominator h_k = a_{i,k}^H R_k^-1 a_{i,k} (Sec. III-C, Sec. III-D,
+// eq. ASSC0): MF (1/K) sum d_k, MVDR C K / sum h_k, ASSC C / max h_k.
+// FP64, snapshot order fixed.
+__global__ void k_snapshot_image(SnapPtrs sp, int K, int Q, int kind, double C, double *out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Q; i += gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        if (kind == IMG_SNAP_MF) {
+            for (int k = 0; k < K; ++k) acc += (double)sp.d[k][i];
+            out[i] = acc / (double)K;
+        } else if (kind == IMG_SNAP_MVDR) {
+            for (int k = 0; k < K; ++k) acc += (double)sp.h[k][i];
+            out[i] = (C * (double)K) / acc;
+        } else {
+            for (int k = 0; k < K; ++k) acc = fmax(acc, (double)sp.h[k][i]);
+            out[i] = C / acc;
+        }
+    }
+}
+
+cudaError_t launch_snapshot_image(const SnapPtrs &sp, int K, int Q, int kind, double C, double *out,
+                                  cudaStream_t st) {
+    k_snapshot_image<<<min(1024, (Q + 255) / 256), 256, 0, st>>>(sp, K, Q, kind, C, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_to_double(const float *src, double *dst, int n, cudaStream_t st) {
     k_to_double<<<min(1024, (n + 255) / 256 + 1), 256, 0, st>>>(src, dst, n);
     return cudaGetLastError();
