@@ -256,6 +256,25 @@ enum { IMG_SNAP_MF = 0, IMG_SNAP_MVDR = 1, IMG_SNAP_ASSC = 2 };
 #define IMG_MAX_SNAPSHOTS 32
 img_status img_snapshot_image(img_ctx *const *snap, int K, int kind, double *out, int on_device);
 
+/* Unconstrained LS / WLS image over K snapshots (Sec. II stacked model,
+ * eq. vectRtotal; Sec. III-B/C images; Sec. V-A LSQR), every pixel free:
+ * min over x of sum_k ||b_k - M_k x||^2 with, per snapshot k (context
+ * snap[k]), M_k = Psi_k, b_k = vect(R_hat_k) (IMG_COST_LS) or
+ * M_k = W_k Psi_k D^-1, b_k = W_k vect(R_hat_k), W_k = conj(L_k^-1) kron L_k^-1
+ * (IMG_COST_PWLS), D = diag((sum_k h_{i,k})^2 / (K C)) (eq. D), sigma = D^-1 x.
+ * The weighting acts on each snapshot's block (the paper writes it with the
+ * block-diagonal R_hat).  LSQR as in img_ls_image: device-side Golub-Kahan
+ * over the K blocks of u (one p x p block per snapshot), the snapshots'
+ * operators run one after another on snap[0]'s stream and M^H u sums them in
+ * snapshot order; snap[0]'s lsqr_atol / lsqr_btol, tests every 10
+ * iterations, maxit <= 0: 200.  The contexts must satisfy the conditions of
+ * img_snapshot_image and share the cost.  Each call allocates its work
+ * buffers (2 K p^2 complex + O(Q)) and frees them before returning.
+ * sigma[0..Q) host or device per on_device; info as in img_ls_image with
+ * op_flops summed over the snapshots. */
+img_status img_snapshot_ls_image(img_ctx *const *snap, int K, int maxit, double *sigma, img_solve_info *info,
+                                 int on_device);
+
 /* Factor R_hat, dirty images and bounds of several jobs in single launches
  * (the step img_solve_batch would otherwise run first).  Every context must
  * hold a covariance and use the same device; runs on ctxs[0]'s stream.

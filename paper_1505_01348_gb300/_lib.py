@@ -26,7 +26,7 @@ SET_L, SET_U, SET_F = 0, 1, 2
 EXPORTS = ("img_params_default", "img_create", "img_set_covariance", "img_dirty",
            "img_mvdr_bound", "img_solve", "img_get_sets", "img_get_gradient", "img_get_events",
            "img_psi",
-           "img_psi_adj", "img_ls_image", "img_check_wait", "img_snapshot_image", "img_prepare_batch", "img_solve_batch", "img_psi_noalloc",
+           "img_psi_adj", "img_ls_image", "img_check_wait", "img_snapshot_image", "img_snapshot_ls_image", "img_prepare_batch", "img_solve_batch", "img_psi_noalloc",
            "img_server_params_default", "img_server_create", "img_server_reserve", "img_server_submit",
            "img_server_wait", "img_server_destroy", "img_destroy", "img_status_str")
 
@@ -103,6 +103,8 @@ def load(build_if_missing: bool = False) -> C.CDLL:
     lib.img_check_wait.argtypes = [C.c_uint, i]
     lib.img_snapshot_image.restype = i
     lib.img_snapshot_image.argtypes = [C.POINTER(vp), i, i, dp, i]
+    lib.img_snapshot_ls_image.restype = i
+    lib.img_snapshot_ls_image.argtypes = [C.POINTER(vp), i, i, dp, C.POINTER(SolveInfo), i]
     lib.img_check_wait.restype = i
     lib.img_get_sets.argtypes = [vp, dp]
     lib.img_get_sets.restype = i
@@ -343,6 +345,20 @@ def snapshot_image(imagers, kind=None, out=None):
     code = lib.img_snapshot_image(hs, n, kind, _ptr(out), 1 if _is_device(out) else 0)
     _check(code, "img_snapshot_image")
     return out
+
+
+def snapshot_ls_image(imagers, maxit=0, out=None):
+    """Unconstrained LS / WLS image over K snapshots, one Imager per snapshot
+    (img_snapshot_ls_image); returns (image, SolveInfo)."""
+    lib = load()
+    n = len(imagers)
+    if out is None:
+        out = np.empty(imagers[0].Q if n else 0, dtype=np.float64)
+    hs = (C.c_void_p * max(n, 1))(*[im.h.value for im in imagers])
+    info = SolveInfo()
+    code = lib.img_snapshot_ls_image(hs, n, int(maxit), _ptr(out), C.byref(info), 1 if _is_device(out) else 0)
+    _check(code, "img_snapshot_ls_image")
+    return out, info
 
 
 def solve_batch(imagers, outs=None, allow=(IMG_ENOTCONV,)):

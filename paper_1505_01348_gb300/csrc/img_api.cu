@@ -544,13 +544,17 @@ img_status img_psi_adj(img_ctx *c, const double *U, double *out, int on_device) 
     return copy_out_double(c, c->outd, out, Q, 0);
 }
 
-img_status img_snapshot_image(img_ctx *const *snap, int K, int kind, double *out, int on_device) {
-    const Range range_("img.snapshot_image");
-    if (!snap || !out || K < 1 || K > IMG_MAX_SNAPSHOTS) return IMG_EINVAL;
-    if (kind != IMG_SNAP_MF && kind != IMG_SNAP_MVDR && kind != IMG_SNAP_ASSC) return IMG_EINVAL;
+}  // extern "C"
+
+namespace {
+
+// The snapshot entry points take one context per snapshot: all hold a
+// covariance and agree on device, p, grid, wavelength, N and bias constant.
+img_status check_snapshots(img_ctx *const *snap, int K) {
+    if (!snap || K < 1 || K > IMG_MAX_SNAPSHOTS) return IMG_EINVAL;
     for (int k = 0; k < K; ++k)
         if (!snap[k] || !snap[k]->has_cov) return IMG_EINVAL;
-    img_ctx *c0 = snap[0];
+    const img_ctx *c0 = snap[0];
     for (int k = 1; k < K; ++k) {
         const img_ctx *c = snap[k];
         if (c->device != c0->device || c->prm.p != c0->prm.p || c->prm.n_l != c0->prm.n_l ||
@@ -558,6 +562,28 @@ img_status img_snapshot_image(img_ctx *const *snap, int K, int kind, double *out
             c->prm.bias_c != c0->prm.bias_c || c->hj.N != c0->hj.N || c->l != c0->l || c->m != c0->m)
             return IMG_EINVAL;
     }
+    return IMG_OK;
+}
+
+// Device allocation freed on scope exit (every return path).
+struct DevBuf {
+    void *ptr = nullptr;
+    ~DevBuf() {
+        if (ptr) cudaFree(ptr);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+img_status img_snapshot_image(img_ctx *const *snap, int K, int kind, double *out, int on_device) {
+    const Range range_("img.snapshot_image");
+    if (!out) return IMG_EINVAL;
+    if (kind != IMG_SNAP_MF && kind != IMG_SNAP_MVDR && kind != IMG_SNAP_ASSC) return IMG_EINVAL;
+    const img_status chk = check_snapshots(snap, K);
+    if (chk != IMG_OK) return chk;
+    img_ctx *c0 = snap[0];
     for (int k = 0; k < K; ++k) {
         const img_status st = prepare(snap[k]);     // synchronises snapshot k's stream
         if (st != IMG_OK) return st;
@@ -574,6 +600,117 @@ img_status img_snapshot_image(img_ctx *const *snap, int K, int kind, double *out
     CK(img::launch_snapshot_image(sp, K, Q, kind, C, on_device ? out : c0->outd, c0->stream));
     if (on_device) return sync(c0);
     return copy_out_double(c0, c0->outd, out, Q, 0);
+}
+
+img_status img_snapshot_ls_image(img_ctx *const *snap, int K, int maxit, double *sigma, img_solve_info *info,
+                                 int on_device) {
+    const Range range_("img.snapshot_ls_image");
+    if (!sigma) return IMG_EINVAL;
+    img_status st = check_snapshots(snap, K);
+    if (st != IMG_OK) return st;
+    img_ctx *c0 = snap[0];
+    for (int k = 1; k < K; ++k)
+        if (snap[k]->prm.cost != c0->prm.cost) return IMG_EINVAL;
+    for (int k = 0; k < K; ++k) {
+        st = prepare(snap[k]);
+        if (st != IMG_OK) return st;
+        if (op_mode_of(snap[k]) != 0 && !snap[k]->fwd_part) {
+            int sms = 1;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, snap[k]->device);
+            CK(cudaMalloc(&snap[k]->fwd_part, img::psi_wide_part_floats(sms) * sizeof(float)));
+        }
+    }
+    const int Q = c0->hj.Q, p = c0->prm.p, pp = p * p;
+    // K blocks of u and M v, shared p x p scratch, Q-vectors v, w, x, wx and
+    // the K-snapshot scale, y / yk / sigma staging, scalars: one allocation
+    // for the call
+    auto al = [](size_t n) { return (n + 255) / 256 * 256; };
+    const size_t need = 2 * al((size_t)K * pp * sizeof(float2)) + 2 * al((size_t)pp * sizeof(float2)) +
+                        al((size_t)pp * sizeof(double2)) + 5 * al((size_t)Q * sizeof(float)) +
+                        3 * al((size_t)Q * sizeof(double)) + al(img::kLsScalars * sizeof(double));
+    DevBuf mem;
+    CK(cudaMalloc(&mem.ptr, need));
+    char *m = static_cast<char *>(mem.ptr);
+    auto take = [&](size_t n) {
+        char *r = m;
+        m += al(n);
+        return r;
+    };
+    img::LsBufs b;
+    b.u = reinterpret_cast<float2 *>(take((size_t)K * pp * sizeof(float2)));
+    b.Mv = reinterpret_cast<float2 *>(take((size_t)K * pp * sizeof(float2)));
+    b.T1 = reinterpret_cast<float2 *>(take((size_t)pp * sizeof(float2)));
+    b.Uw = reinterpret_cast<float2 *>(take((size_t)pp * sizeof(float2)));
+    b.Kd = reinterpret_cast<double2 *>(take((size_t)pp * sizeof(double2)));
+    b.v = reinterpret_cast<float *>(take((size_t)Q * sizeof(float)));
+    b.w = reinterpret_cast<float *>(take((size_t)Q * sizeof(float)));
+    b.x = reinterpret_cast<float *>(take((size_t)Q * sizeof(float)));
+    b.wx = reinterpret_cast<float *>(take((size_t)Q * sizeof(float)));
+    float *scale = reinterpret_cast<float *>(take((size_t)Q * sizeof(float)));
+    b.y = reinterpret_cast<double *>(take((size_t)Q * sizeof(double)));
+    double *yk = reinterpret_cast<double *>(take((size_t)Q * sizeof(double)));
+    double *sig = reinterpret_cast<double *>(take((size_t)Q * sizeof(double)));
+    b.sc = reinterpret_cast<double *>(take(img::kLsScalars * sizeof(double)));
+
+    img::SnapPtrs sp{};
+    img::LsSnap s;
+    s.K = K;
+    s.yk = yk;
+    for (int k = 0; k < K; ++k) {
+        sp.d[k] = snap[k]->hj.dirty;
+        sp.h[k] = snap[k]->hj.h;
+        s.jd[k] = snap[k]->dj;
+        s.hj[k] = snap[k]->hj;
+        s.hj[k].scale = scale;
+        s.mode[k] = op_mode_of(snap[k]);
+        s.fwd_part[k] = snap[k]->fwd_part;
+        s.part[k] = snap[k]->part;
+        s.nparts[k] = snap[k]->nparts;
+    }
+    const long long N = c0->hj.N;
+    const double C = c0->prm.bias_c ? (double)N / (double)(N - p) : 1.0;
+    cudaStream_t stream = c0->stream;
+    const auto t0 = std::chrono::steady_clock::now();
+    CK(img::launch_snap_scale(sp, K, Q, c0->prm.cost == IMG_COST_PWLS, C, scale, stream));
+    CK(img::ls_snap_begin(s, b, stream));
+    const int lim = maxit > 0 ? maxit : 200;
+    const double atol = c0->prm.lsqr_atol, btol = c0->prm.lsqr_btol;
+    int it = 0, istop = 3;
+    double h[img::kLsScalars] = {};
+    for (it = 1; it <= lim; ++it) {
+        CK(img::ls_snap_iterate(s, b, stream));
+        if (it % 10 == 0 || it == lim) {
+            // Paige-Saunders stopping tests on the host, every 10 iterations
+            CK(img::ls_xnorm2(s.hj[0], b, b.sc + img::kLsXnorm2, stream));
+            CK(cudaMemcpyAsync(h, b.sc, sizeof(h), cudaMemcpyDeviceToHost, stream));
+            CK(cudaStreamSynchronize(stream));
+            const double anorm = std::sqrt(h[img::kLsAnorm2]), xnorm = std::sqrt(h[img::kLsXnorm2]);
+            if (h[img::kLsRnorm] <= btol * h[img::kLsBnorm] + atol * anorm * xnorm) {
+                istop = 1;
+                break;
+            }
+            if (h[img::kLsArnorm] <= atol * anorm * h[img::kLsRnorm]) {
+                istop = 2;
+                break;
+            }
+        }
+    }
+    if (it > lim) it = lim;
+    CK(img::ls_finish(s.hj[0], b, on_device ? sigma : sig, nullptr, stream));
+    if (!on_device) CK(cudaMemcpyAsync(sigma, sig, (size_t)Q * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info) {
+        std::memset(info, 0, sizeof(*info));
+        info->status = IMG_OK;
+        info->lsqr_iters = it;
+        info->n_free = Q;
+        info->converged = istop < 3 ? 1 : 0;
+        info->lambda_min = h[img::kLsRnorm];
+        info->op_flops = ((double)(it + 1) * 8.0 * pp * Q + (double)it * 4.0 * pp * Q) * K;
+        info->t_end_ns = secs * 1e9;
+    }
+    return IMG_OK;
 }
 
 img_status img_check_wait(unsigned polls, int arrive) {

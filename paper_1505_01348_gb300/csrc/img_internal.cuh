@@ -133,6 +133,31 @@ cudaError_t ls_iterate(const JobDev *jd, const JobDev &hj, LsBufs &b, int mode, 
 cudaError_t ls_finish(const JobDev &hj, LsBufs &b, double *sigma, double *xnorm2, cudaStream_t st);
 cudaError_t ls_xnorm2(const JobDev &hj, LsBufs &b, double *out, cudaStream_t st);
 
+// Per-snapshot arrays for the K-snapshot dirty images (passed by value).
+struct SnapPtrs {
+    const float *d[IMG_MAX_SNAPSHOTS];   // MF dirty image of snapshot k
+    const float *h[IMG_MAX_SNAPSHOTS];   // a^H R_k^-1 a of snapshot k
+};
+// Full-image LSQR over K snapshots (stacked operator of Sec. II, eq.
+// vectRtotal): u holds K blocks of p x p (b.u and b.Mv have K * p^2
+// entries), v, w, x are shared, M^H u sums the snapshots' adjoints in
+// snapshot order.  hj[k] is snapshot k's host mirror with scale replaced by
+// the K-snapshot scale (1/D of eq. D for PWLS, 1 for CLS); snapshots run one
+// after another on the given stream, sharing the scratch in b.
+struct LsSnap {
+    int K = 0;
+    const JobDev *jd[IMG_MAX_SNAPSHOTS] = {};
+    JobDev hj[IMG_MAX_SNAPSHOTS] = {};
+    int mode[IMG_MAX_SNAPSHOTS] = {};
+    float *fwd_part[IMG_MAX_SNAPSHOTS] = {};
+    float2 *part[IMG_MAX_SNAPSHOTS] = {};
+    int nparts[IMG_MAX_SNAPSHOTS] = {};
+    double *yk = nullptr;      // Q doubles: one snapshot's M_k^H u_k
+};
+cudaError_t ls_snap_begin(const LsSnap &s, LsBufs &b, cudaStream_t st);
+cudaError_t ls_snap_iterate(const LsSnap &s, LsBufs &b, cudaStream_t st);
+cudaError_t launch_snap_scale(const SnapPtrs &sp, int K, int Q, int pwls, double C, float *scale, cudaStream_t st);
+
 // Wide tensor-core forward K = Psi w (64 < p <= 256, mode 1 or 2): wbits is
 // a device word (cleared here), part a scratch of psi_wide_part_floats(SMs)
 // floats; Kout p x p complex128.
@@ -150,11 +175,6 @@ cudaError_t launch_z2c(const double2 *src, float2 *dst, int n, cudaStream_t st);
 cudaError_t launch_c2z(const float2 *src, double2 *dst, int n, cudaStream_t st);
 cudaError_t launch_d2f(const double *src, float *dst, int n, cudaStream_t st);
 cudaError_t launch_to_double(const float *src, double *dst, int n, cudaStream_t st);
-// Per-snapshot arrays for the K-snapshot dirty images (passed by value).
-struct SnapPtrs {
-    const float *d[IMG_MAX_SNAPSHOTS];   // MF dirty image of snapshot k
-    const float *h[IMG_MAX_SNAPSHOTS];   // a^H R_k^-1 a of snapshot k
-};
 cudaError_t launch_snapshot_image(const SnapPtrs &sp, int K, int Q, int kind, double C, double *out,
                                   cudaStream_t st);
 

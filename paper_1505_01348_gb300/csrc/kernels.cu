@@ -1628,6 +1628,95 @@ cudaError_t ls_iterate(const JobDev *jd, const JobDev &hj, LsBufs &b, int mode, 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- K-snapshot full-image LSQR
+// y = first ? yk : y + yk (the snapshot sum of M^H u, snapshot order fixed).
+__global__ void k_ls_accum(double *y, const double *yk, int Q, int first) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Q; i += gridDim.x * blockDim.x)
+        y[i] = first ? yk[i] : y[i] + yk[i];
+}
+
+// Pixel scale of the K-snapshot solver variable: 1/D with
+// D = (sum_k h_k)^2 / (K C) for PWLS (eq. D), 1 for CLS.
+__global__ void k_snap_scale(SnapPtrs sp, int K, int Q, int pwls, double C, float *scale) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Q; i += gridDim.x * blockDim.x) {
+        double hs = 0.0;
+        for (int k = 0; k < K; ++k) hs += (double)sp.h[k][i];
+        scale[i] = pwls ? (float)(1.0 / ((hs * hs) / ((double)K * C))) : 1.0f;
+    }
+}
+
+cudaError_t launch_snap_scale(const SnapPtrs &sp, int K, int Q, int pwls, double C, float *scale, cudaStream_t st) {
+    k_snap_scale<<<ls_grid(Q), kThreads, 0, st>>>(sp, K, Q, pwls, C, scale);
+    return cudaGetLastError();
+}
+
+// Buffers of snapshot k: its block of u and M v, the shared scratch, and the
+// per-snapshot adjoint output yk.
+static LsBufs snap_bufs(const LsSnap &s, const LsBufs &b, int k) {
+    LsBufs bk = b;
+    const size_t pp = (size_t)s.hj[0].p * s.hj[0].p;
+    bk.u = b.u + (size_t)k * pp;
+    bk.Mv = b.Mv + (size_t)k * pp;
+    bk.y = s.yk;
+    return bk;
+}
+
+// y = sum_k M_k^H u_k.
+static cudaError_t snap_adjoint(const LsSnap &s, LsBufs &b, cudaStream_t st) {
+    const int Q = s.hj[0].Q;
+    for (int k = 0; k < s.K; ++k) {
+        LsBufs bk = snap_bufs(s, b, k);
+        cudaError_t e = ls_adjoint(s.jd[k], s.hj[k], bk, s.mode[k], st);
+        if (e != cudaSuccess) return e;
+        k_ls_accum<<<ls_grid(Q), kThreads, 0, st>>>(b.y, s.yk, Q, k == 0);
+    }
+    return cudaGetLastError();
+}
+
+// M_k v into block k of b.Mv for every snapshot.
+static cudaError_t snap_forward(const LsSnap &s, LsBufs &b, cudaStream_t st) {
+    for (int k = 0; k < s.K; ++k) {
+        LsBufs bk = snap_bufs(s, b, k);
+        cudaError_t e = ls_forward(s.jd[k], s.hj[k], bk, s.mode[k], s.fwd_part[k], s.part[k], s.nparts[k], st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t ls_snap_begin(const LsSnap &s, LsBufs &b, cudaStream_t st) {
+    const int Q = s.hj[0].Q, p = s.hj[0].p, pp = p * p, n = s.K * pp;
+    const int pwls = s.hj[0].cost == IMG_COST_PWLS;
+    for (int k = 0; k < s.K; ++k)
+        k_ls_init_u<<<ls_grid(pp), kThreads, 0, st>>>(s.hj[k].R32, p, pwls, b.u + (size_t)k * pp);
+    k_sumsq<<<1, 1024, 0, st>>>(reinterpret_cast<const float *>(b.u), 2 * n, b.sc + kLsSsU);
+    k_ls_scalar<<<1, 32, 0, st>>>(b.sc, 0);
+    k_ls_scale_u<<<ls_grid(n), kThreads, 0, st>>>(b.u, n, b.sc);
+    cudaError_t e = snap_adjoint(s, b, st);
+    if (e != cudaSuccess) return e;
+    k_ls_v<<<ls_grid(Q), kThreads, 0, st>>>(b.v, b.y, s.hj[0].scale, Q, b.sc, 1);
+    k_sumsq<<<1, 1024, 0, st>>>(b.v, Q, b.sc + kLsSsV);
+    k_ls_scalar<<<1, 32, 0, st>>>(b.sc, 1);
+    k_ls_xw<<<ls_grid(Q), kThreads, 0, st>>>(b.x, b.w, b.v, Q, b.sc, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t ls_snap_iterate(const LsSnap &s, LsBufs &b, cudaStream_t st) {
+    const int Q = s.hj[0].Q, pp = s.hj[0].p * s.hj[0].p, n = s.K * pp;
+    cudaError_t e = snap_forward(s, b, st);
+    if (e != cudaSuccess) return e;
+    k_ls_u<<<ls_grid(n), kThreads, 0, st>>>(b.u, b.Mv, n, b.sc);
+    k_sumsq<<<1, 1024, 0, st>>>(reinterpret_cast<const float *>(b.u), 2 * n, b.sc + kLsSsU);
+    k_ls_scalar<<<1, 32, 0, st>>>(b.sc, 2);
+    k_ls_scale_u<<<ls_grid(n), kThreads, 0, st>>>(b.u, n, b.sc);
+    e = snap_adjoint(s, b, st);
+    if (e != cudaSuccess) return e;
+    k_ls_v<<<ls_grid(Q), kThreads, 0, st>>>(b.v, b.y, s.hj[0].scale, Q, b.sc, 0);
+    k_sumsq<<<1, 1024, 0, st>>>(b.v, Q, b.sc + kLsSsV);
+    k_ls_scalar<<<1, 32, 0, st>>>(b.sc, 3);
+    k_ls_xw<<<ls_grid(Q), kThreads, 0, st>>>(b.x, b.w, b.v, Q, b.sc, 0);
+    return cudaGetLastError();
+}
+
 cudaError_t ls_finish(const JobDev &hj, LsBufs &b, double *sigma, double *xnorm2, cudaStream_t st) {
     k_ls_sigma<<<ls_grid(hj.Q), kThreads, 0, st>>>(b.x, hj.scale, sigma, hj.Q);
     if (xnorm2) k_sumsq<<<1, 1024, 0, st>>>(b.x, hj.Q, xnorm2);

@@ -1,7 +1,8 @@
-"""K > 1 snapshots on the GPU: the MF, MVDR and ASSC dirty images over K
-snapshots (img_snapshot_image) against the K-snapshot FP64 oracle, with the
-array turned between snapshots and one covariance per snapshot (Sec. II,
-Sec. III-C, Sec. III-D, eq. ASSC0)."""
+"""K > 1 snapshots on the GPU against the K-snapshot FP64 oracle, with the
+array turned between snapshots and one covariance per snapshot (Sec. II):
+the MF, MVDR and ASSC dirty images over K snapshots (img_snapshot_image;
+Sec. III-C, Sec. III-D, eq. ASSC0) and the unconstrained LS / WLS image of
+the stacked model (img_snapshot_ls_image; Sec. III-B/C, Sec. V-A LSQR)."""
 import numpy as np
 import pytest
 
@@ -118,3 +119,67 @@ def test_snapshot_image_argument_errors(G):
     assert np.all(np.isfinite(out)) and np.all(out > 0)
     for im in ims:
         im.close()
+
+
+# ---------------------------------------------------------------- K-snapshot LS / WLS image
+def _oracle_ls(job, cost):
+    """The K-snapshot oracle's LSQR on the explicit stacked operator (FP64,
+    tolerances 1e-12): full column rank, so the LS / WLS image is unique."""
+    As = S.steering_stack(job.ant_xyz, job.l, job.m, job.lam)
+    Psi = S.khatri_rao_stack(As)
+    bnd = S.bounds_k(As, Psi, job.R, job.N, O.Params(cost=cost))
+    prob = S.cost_problem_k(As, Psi, job.R, bnd, cost)
+    res = O.lsqr(prob.M, prob.b, 1e-12, 1e-12, 2000)
+    assert res.istop in (1, 2)
+    return prob, prob.to_sigma * res.x
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("cost", [0, 1])
+@pytest.mark.parametrize("shape", [(16, 8, 8, 2), (24, 12, 10, 3)])
+def test_snapshot_ls_image_matches_oracle(G, shape, cost, prec):
+    p, nl, nm, K = shape
+    job = synth.snapshots_custom(60 + p, p, nl, nm, 3, 20 * p, K, dtheta=0.3, radius=4.0, snr_db=5.0)
+    prob, ref = _oracle_ls(job, cost)
+    ims = _imagers(G, job, cost=cost, precision=prec, lsqr_atol=1e-7, lsqr_btol=1e-7)
+    _set_cov(ims, job)
+    sigma, info = G.snapshot_ls_image(ims, maxit=600)
+    for im in ims:
+        im.close()
+    assert info.converged == 1
+    tol = 1e-4 if prec != 2 else 1e-3
+    assert _rel(sigma, ref) <= tol
+    # optimality of the GPU image in FP64 on the stacked operator
+    x = sigma / prob.to_sigma
+    g = np.real(prob.M.conj().T @ (prob.b - prob.M @ x))
+    g0 = np.real(prob.M.conj().T @ prob.b)
+    assert np.linalg.norm(g) <= 10 * tol * np.linalg.norm(g0)
+
+
+def test_snapshot_ls_image_one_snapshot_equals_ls_image(G):
+    job = synth.custom(45, 20, 10, 9, 3, 400, radius=4.0, snr_db=5.0)
+    for cost in (0, 1):
+        im = G.Imager.from_job(job, cost=cost, precision=1, lsqr_atol=1e-7, lsqr_btol=1e-7)
+        a, ia = im.ls_image(maxit=300)
+        b, ib = G.snapshot_ls_image([im], maxit=300)
+        im.close()
+        assert abs(ia.lsqr_iters - ib.lsqr_iters) <= 10
+        assert _rel(b, a) <= 1e-5
+
+
+def test_snapshot_ls_image_errors(G):
+    job = synth.snapshots_custom(54, 12, 8, 8, 2, 300, 2)
+    a = G.Imager(job.ant_xyz[0], job.l, job.m, job.lam, cost=0)
+    b = G.Imager(job.ant_xyz[1], job.l, job.m, job.lam, cost=1)
+    a.set_covariance(job.R[0], job.N)
+    with pytest.raises(G.ImgError) as e:
+        G.snapshot_ls_image([a, b])              # b holds no covariance
+    assert e.value.code == G.IMG_EINVAL
+    b.set_covariance(job.R[1], job.N)
+    with pytest.raises(G.ImgError) as e:
+        G.snapshot_ls_image([a, b])              # different costs
+    assert e.value.code == G.IMG_EINVAL
+    b.close()
+    out, info = G.snapshot_ls_image([a, a], maxit=40)
+    assert np.all(np.isfinite(out)) and 1 <= info.lsqr_iters <= 40
+    a.close()
