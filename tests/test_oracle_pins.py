@@ -313,3 +313,40 @@ def test_monte_carlo_bias_and_variances():
     assert abs(mf.mean() / true_mf - 1.0) < 0.005
     assert abs(mf.std() / (true_mf / math.sqrt(N)) - 1.0) < 0.06
     assert abs(mv.std() / (true_mv / math.sqrt(N - p - 1)) - 1.0) < 0.06
+
+
+# ---------------------------------------------------------------- degenerate cases
+@pytest.mark.parametrize("cost", [O.COST_LS, O.COST_PWLS])
+@pytest.mark.parametrize("bound", [O.BOUND_MF, O.BOUND_MVDR])
+def test_single_pixel_closed_form(cost, bound):
+    """Q = 1: the bounded problem is a scalar least squares clipped to
+    [0, gamma].  With ||a|| = 1 the CLS minimiser is a^H R a (the dirty image)
+    and the WLS minimiser is 1 / (a^H R^-1 a) (the MVDR image, C = 1); both
+    exceed or equal the MVDR bound, so with that bound the image is the bound,
+    and with the MF bound it is the unclipped minimiser."""
+    job = synth.custom(81, 5, 1, 1, 1, 400, radius=2.0)
+    a = O.steering_matrix(job.ant_xyz, job.l, job.m, job.lam)[:, 0]
+    d = float(np.real(a.conj() @ job.R @ a))
+    mv = 1.0 / float(np.real(a.conj() @ np.linalg.solve(job.R, a)))
+    prm = O.Params(cost=cost, bound=bound, kappa=0.0, eps_floor=1e-12, feas_tol=1e-9)
+    res = O.image_job(job, prm)
+    assert res.solve.converged
+    if bound == O.BOUND_MVDR:
+        expect = mv
+    else:
+        expect = d if cost == O.COST_LS else mv
+    assert abs(res.solve.sigma[0] - expect) <= 1e-9 * expect
+    assert res.solve.events[0] == ("free", 0)
+
+
+def test_two_antenna_array():
+    """p = 2, the smallest array: the bounds and an exact solve agree with
+    dense BVLS on the explicit operator."""
+    job = synth.custom(82, 2, 3, 2, 1, 300, radius=1.0, snr_db=5.0)
+    for cost in (O.COST_LS, O.COST_PWLS):
+        prm = O.Params(cost=cost, kappa=0.0, eps_floor=1e-11)
+        bnd, prob = _problem(job, cost, prm)
+        assert np.all(bnd.mvdr <= bnd.dirty * (1 + 1e-12))
+        res = O.active_set(prob, bnd.eps, prm)
+        assert res.converged
+        _kkt_ok(prob, res, 1e-8)
