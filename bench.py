@@ -332,6 +332,49 @@ def run_ls_images(args, iters: int = 100):
     return out
 
 
+def run_snapshots(args, iters: int = 100):
+    """K > 1 snapshots on the stand-in for the paper's extended-source
+    simulation (p = 100 antennas in a disk, K = 2 snapshots with the array
+    turned 0.05 rad between them, 64x64 grid, a point source and two extended
+    structures, N = 10^4): the K-snapshot MF, MVDR and ASSC images
+    (img_snapshot_image, including both snapshots' factor and bounds, which a
+    new covariance clears) and the K-snapshot WLS image
+    (img_snapshot_ls_image, a fixed 100 LSQR iterations, stopping tolerances
+    0).  Wall time per call, best of 3."""
+    import paper_1505_01348_gb300 as G
+    import synth
+
+    prec = PRECISIONS[args.precision]
+    job = synth.snapshots_extended()
+    out = {"workload": "p=100 disk, K=2 snapshots (0.05 rad apart), 64x64 grid, point + 2 extended "
+                       "structures, N=1e4, pwls", "precision": args.precision}
+    ims = [G.Imager(job.ant_xyz[k], job.l, job.m, job.lam, precision=prec, lsqr_atol=0.0, lsqr_btol=0.0)
+           for k in range(job.K)]
+    try:
+        ts = []
+        for _ in range(3):
+            for k, im in enumerate(ims):
+                im.set_covariance(job.R[k], job.N)
+            t0 = time.perf_counter()
+            for kind in (G.SNAP_MF, G.SNAP_MVDR, G.SNAP_ASSC):
+                G.snapshot_image(ims, kind)
+            ts.append(time.perf_counter() - t0)
+        out["images_mf_mvdr_assc_s"] = min(ts)
+        G.snapshot_ls_image(ims, maxit=5)              # warm-up (kernel attributes, scratch)
+        ts = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            _, info = G.snapshot_ls_image(ims, maxit=iters)
+            ts.append(time.perf_counter() - t0)
+        t = min(ts)
+        out["ls_image"] = {"s_per_image": t, "images_s": 1.0 / t, "lsqr_iters": info.lsqr_iters,
+                           "useful_operator_tflops": info.op_flops / t / 1e12}
+    finally:
+        for im in ims:
+            im.close()
+    return out
+
+
 def _steer64(ant, l, m, lam, il, im):
     """FP64 steering vectors of pixels (il, im), unit norm, -j sign (the data
     model's definition; host check values, no oracle code)."""
@@ -632,6 +675,11 @@ def main():
             line["serve"] = run_serve(args)
         if not args.no_cpu and world == 1:
             line["cpu_baseline"] = cpu_baseline_line(oracle_passes_per_image())
+        if not args.no_ops and world == 1:
+            try:
+                line["snapshots"] = run_snapshots(args)
+            except Exception as e:                   # reported in the line, never fatal
+                line["snapshots"] = {"error": f"{type(e).__name__}: {e}"}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()
