@@ -31,8 +31,11 @@
  *   - Calls on one context are not thread-safe; separate contexts are
  *     independent.  Every call returns after its results are in the
  *     caller's buffer (it synchronises the context's stream), except
- *     img_set_covariance with on_device = 1, which only enqueues the copy.
+ *     img_set_covariance with on_device = 1, which only enqueues the copy,
+ *     and img_psi / img_psi_adj with on_device = 2 (stream-ordered).
  *   - No C++ exception crosses this boundary; failures are status codes.
+ *   - K > 1 snapshots (Sec. II): one context per snapshot, combined by
+ *     img_snapshot_image and img_snapshot_ls_image.
  */
 #ifndef IMG_GB300_H
 #define IMG_GB300_H
