@@ -326,3 +326,35 @@ def test_monte_carlo_k_snapshot_variances():
     # the per-draw estimates scatter around the same values
     assert abs(np.mean(std_mf) / sd_mf - 1.0) < 0.02
     assert abs(np.mean(std_mv) / sd_mv - 1.0) < 0.03
+
+
+def test_mvdr_alpha_and_upper_bound_chain_with_true_covariances():
+    """Sec. III-D (eq. MVDRUB2): alpha = w^H (I_K o A^i)(I_K o A^i)^H w >= 1 for
+    the MVDR beamformer, computed with dense matrices and equal to
+    K sum_k h_k^2 / (sum_k h_k)^2; hence with the true covariances
+    R_k = sum_q s_q a_{q,k} a_{q,k}^H + n I every bound sits above the true
+    sky: sigma <= ASSC <= MVDR <= MF at every pixel (C = 1)."""
+    K, p, n_l, n_m = 3, 8, 7, 6
+    job = synth.snapshots_custom(95, p, n_l, n_m, 4, 1000, K, dtheta=0.4, radius=5.0)
+    As = S.steering_stack(job.ant_xyz, job.l, job.m, job.lam)
+    Psi = S.khatri_rao_stack(As)
+    s = job.sigma_true
+    Rt = np.stack([(As[k] * s[None, :]) @ As[k].conj().T + job.noise_var * np.eye(p) for k in range(K)])
+    bnd = S.bounds_k(As, Psi, Rt, 1000, O.Params(bias_c=0))
+    R = sla.block_diag(*Rt)
+    Rinv = np.linalg.inv(R)
+    for i in range(job.Q):
+        a = _long(As, i)
+        w = math.sqrt(K) * (Rinv @ a) / np.real(np.vdot(a, Rinv @ a))
+        V = _ik_circ(As, i)
+        alpha = float(np.real(np.vdot(w, V @ (V.conj().T @ w))))
+        h = bnd.hk[:, i]
+        assert alpha >= 1.0 - 1e-12
+        assert abs(alpha - K * np.sum(h * h) / np.sum(h) ** 2) <= 1e-10 * alpha
+    tol = 1e-12 * np.max(bnd.dirty)
+    assert np.all(s <= bnd.assc + tol)
+    assert np.all(bnd.assc <= bnd.mvdr + tol)
+    assert np.all(bnd.mvdr <= bnd.dirty + tol)
+    # the bounds are not slack everywhere: at a source pixel the MVDR bound is close
+    i = int(np.argmax(s))
+    assert bnd.mvdr[i] < 1.5 * s[i] + job.noise_var
