@@ -17,6 +17,7 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
 import synth                       # noqa: E402
 from oracle import imager as O     # noqa: E402
+from oracle import snapshots as S  # noqa: E402
 
 RECORDS = {
     # 128x128 grid, p = 64 log-spiral, 20 points + Gaussian blob, N = 1e4,
@@ -25,6 +26,12 @@ RECORDS = {
                                                                 eps_floor=1e-6, feas_tol=1e-5)),
     "mid_ls": dict(maker=lambda: synth.mid(), prm=O.Params(cost=O.COST_LS, kappa=6.0,
                                                             eps_floor=1e-6, feas_tol=1e-5)),
+    # K = 2 snapshots, p = 100 disk, 64x64 grid, a point source and two
+    # extended structures (the stand-in for the paper's extended-source
+    # simulation), PWLS with the K-snapshot MVDR bound, kappa = 6
+    "snapshots_extended_pwls": dict(maker=lambda: synth.snapshots_extended(),
+                                    prm=O.Params(cost=O.COST_PWLS, kappa=6.0, eps_floor=1e-6,
+                                                 feas_tol=1e-5)),
 }
 
 
@@ -33,11 +40,13 @@ def make(name: str) -> str:
     job = rec["maker"]()
     prm = rec["prm"]
     t0 = time.time()
-    res = O.image_job(job, prm)
+    snap = hasattr(job, "K")
+    res = S.image_snapshot_job(job, prm) if snap else O.image_job(job, prm)
     dt = time.time() - t0
     out = os.path.join(HERE, f"{name}.npz")
+    extra = dict(assc=res.bounds.assc, K=job.K) if snap else {}
     np.savez_compressed(
-        out, ant_xyz=job.ant_xyz, l=job.l, m=job.m, lam=job.lam, R=job.R, N=job.N,
+        out, **extra, ant_xyz=job.ant_xyz, l=job.l, m=job.m, lam=job.lam, R=job.R, N=job.N,
         cost=prm.cost, kappa=prm.kappa, eps_floor=prm.eps_floor, feas_tol=prm.feas_tol,
         dirty=res.bounds.dirty, mvdr=res.bounds.mvdr, gamma=res.bounds.gamma,
         sigma=res.solve.sigma, sets=res.solve.sets, outer=res.solve.outer,
