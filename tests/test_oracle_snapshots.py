@@ -358,3 +358,19 @@ def test_mvdr_alpha_and_upper_bound_chain_with_true_covariances():
     # the bounds are not slack everywhere: at a source pixel the MVDR bound is close
     i = int(np.argmax(s))
     assert bnd.mvdr[i] < 1.5 * s[i] + job.noise_var
+
+
+def test_stored_k_snapshot_bounds_record_is_the_oracle_output():
+    """tests/golden/snapshots_extended_bounds.npz (written by
+    tests/golden/make_golden.py) holds the seeded stand-in for the paper's
+    extended-source simulation and the oracle's K-snapshot MF, MVDR and
+    ASSC images for it; recomputing them from the stored inputs reproduces
+    the stored values."""
+    import os
+    z = np.load(os.path.join(os.path.dirname(__file__), "golden", "snapshots_extended_bounds.npz"))
+    As = S.steering_stack(z["ant_xyz"], z["l"], z["m"], float(z["lam"]))
+    bnd = S.bounds_k(As, S.khatri_rao_stack(As), z["R"], int(z["N"]), O.Params(bias_c=int(z["bias_c"])))
+    for key in ("dirty", "mvdr", "assc"):
+        np.testing.assert_allclose(getattr(bnd, key), z[key], rtol=1e-12)
+    job = synth.snapshots_extended()
+    np.testing.assert_allclose(job.R, z["R"], rtol=0, atol=1e-12 * np.abs(z["R"]).max())   # the recipe's inputs
