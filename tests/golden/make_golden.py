@@ -30,6 +30,12 @@ RECORDS = {
     # extended structures (the stand-in for the paper's extended-source
     # simulation): the K-snapshot MF, MVDR and ASSC images only (C = 1); the
     # bounded solve of this sky takes the oracle well over an hour
+    # K = 2 snapshots, p = 48 disk of radius 20, 48x48 grid, 15 point sources
+    # U[1, 10], SNR 0 dB, N = 1e4, the array turned 0.2 rad between
+    # snapshots: PWLS with the K-snapshot MVDR bound, kappa = 6
+    "snapshots_mid_pwls": dict(maker=lambda: synth.snapshots_custom(7148, 48, 48, 48, 15, 10_000, 2,
+                                                                    dtheta=0.2, radius=20.0, snr_db=0.0),
+                               prm=O.Params(cost=O.COST_PWLS, kappa=6.0, eps_floor=1e-6, feas_tol=1e-5)),
     "snapshots_extended_bounds": dict(maker=lambda: synth.snapshots_extended(),
                                       prm=O.Params(cost=O.COST_PWLS), bounds_only=True),
 }

@@ -374,3 +374,32 @@ def test_stored_k_snapshot_bounds_record_is_the_oracle_output():
         np.testing.assert_allclose(getattr(bnd, key), z[key], rtol=1e-12)
     job = synth.snapshots_extended()
     np.testing.assert_allclose(job.R, z["R"], rtol=0, atol=1e-12 * np.abs(z["R"]).max())   # the recipe's inputs
+
+
+def test_stored_k_snapshot_solve_record_is_a_relaxed_kkt_point():
+    """tests/golden/snapshots_mid_pwls.npz (K = 2, p = 48, 48x48, PWLS,
+    kappa = 6): the stored bounds are the oracle's for the stored inputs, and
+    the stored image satisfies what Table I guarantees at its exit - feasible
+    (0 <= sigma <= gamma), the free-set gradient near zero and every active
+    pixel's multiplier above -eps (Sec. IV-C)."""
+    import os
+    z = np.load(os.path.join(os.path.dirname(__file__), "golden", "snapshots_mid_pwls.npz"))
+    prm = O.Params(cost=int(z["cost"]), kappa=float(z["kappa"]), eps_floor=float(z["eps_floor"]),
+                   feas_tol=float(z["feas_tol"]))
+    As = S.steering_stack(z["ant_xyz"], z["l"], z["m"], float(z["lam"]))
+    Psi = S.khatri_rao_stack(As)
+    bnd = S.bounds_k(As, Psi, z["R"], int(z["N"]), prm)
+    for key in ("dirty", "mvdr", "assc", "gamma"):
+        np.testing.assert_allclose(getattr(bnd, key), z[key], rtol=1e-12)
+    assert bool(z["converged"])
+    prob = S.cost_problem_k(As, Psi, z["R"], bnd, prm.cost)
+    sigma, sets = z["sigma"], z["sets"]
+    assert np.all(sigma >= 0) and np.all(sigma <= bnd.gamma * (1 + 1e-12))
+    x = sigma / prob.to_sigma
+    g = O.gradient(prob, x)
+    lam = np.where(sets == O.SET_U, -g, g)
+    act = sets != O.SET_F
+    assert np.all(lam[act] >= -bnd.eps[act] * (1 + 1e-9))
+    F = sets == O.SET_F
+    assert np.max(np.abs(g[F])) <= 1e-5 * np.max(np.abs(bnd.mvdr))
+    assert int(F.sum()) == int(np.sum(z["events"][:, 0] == 0)) - int(np.sum(z["events"][:, 0] == 1))
