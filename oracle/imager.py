@@ -21,6 +21,15 @@ image formation using constrained least squares and Krylov subspaces"):
 * LSQR (Paige & Saunders 1982, referenced in Sec. V-A) on the
   Golub-Kahan recurrences eq. initbeta .. eq. lanczos.
 
+Two equivalent forms of the operator are available.  The explicit form builds
+Psi (or M) column by column and multiplies by it; it is the form every pin
+starts from.  The streamed form never stores Psi (Sec. V-B: the operator is
+applied through the steering vectors): Psi x = vect(A diag(x) A^H) and
+Psi^H vect(U) = Re vecdiag(A^H U A), the Khatri-Rao properties of the
+notation section, evaluated on the columns a product needs.  It is what
+makes the 256 x 256, p = 288 workload computable (its explicit Psi would
+hold 87 GB).
+
 Readings where the paper is silent or ambiguous (documented beside each use):
 steering sign -j; K = 1 snapshot; detection threshold eps_i = kappa * std_i
 with a relative floor; ties resolved to the smallest pixel index; cold-start
@@ -91,6 +100,48 @@ def khatri_rao_psi(A: np.ndarray) -> np.ndarray:
     return Psi
 
 
+# Pixels per block in the streamed products: a memory bound only; every
+# pixel's value is computed on its own, so blocking changes no arithmetic.
+STREAM_BLOCK = 4096
+
+
+def psi_apply(A: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """Psi x = vect(A diag(x) A^H) without forming Psi (notation section:
+    (conj(B) o A) x = vect(A diag(x) B^H), here with B = A)."""
+    return vect((A * x[None, :]) @ A.conj().T)
+
+
+def psi_adjoint(A: np.ndarray, U: np.ndarray) -> np.ndarray:
+    """Psi^H vect(U) = Re vecdiag(A^H U A) without forming Psi (notation
+    section: (conj(B) o A)^H vect(U) = vecdiag(A^H U B), here B = A); the
+    imaginary part vanishes for Hermitian U and is dropped explicitly."""
+    Q = A.shape[1]
+    out = np.empty(Q)
+    for i0 in range(0, Q, STREAM_BLOCK):
+        Ab = A[:, i0:i0 + STREAM_BLOCK]
+        out[i0:i0 + Ab.shape[1]] = np.real(np.sum(Ab.conj() * (U @ Ab), axis=0))
+    return out
+
+
+class KhatriRaoCols:
+    """The operator M_S = (conj(B_S) o B_S) diag(dinv_S) on a pixel subset S
+    in streamed form (Sec. V-B): B_S = T A_S with T = I (CLS) or L^{-1}
+    (PWLS, by the mixed-product rule), dinv = 1 (CLS) or 1/D (PWLS).
+      matvec(v)  = vect(B_S diag(dinv_S v) B_S^H)
+      rmatvec(u) = dinv_S * Re vecdiag(B_S^H U B_S),  U = unvect(u)."""
+
+    def __init__(self, B: np.ndarray, dinv: np.ndarray):
+        self.B = B
+        self.dinv = dinv
+        self.shape = (B.shape[0] * B.shape[0], B.shape[1])
+
+    def matvec(self, v: np.ndarray) -> np.ndarray:
+        return psi_apply(self.B, self.dinv * v)
+
+    def rmatvec(self, u: np.ndarray) -> np.ndarray:
+        return self.dinv * psi_adjoint(self.B, unvect(u, self.B.shape[0]))
+
+
 def dirty_mf(Psi: np.ndarray, R: np.ndarray) -> np.ndarray:
     """Matched-filter dirty image, eq. mfdimg: (1/K) Psi^H r_hat, K = 1."""
     return np.real(Psi.conj().T @ vect(R))
@@ -147,6 +198,7 @@ def bounds(A: np.ndarray, Psi: np.ndarray, R: np.ndarray, N: int,
     """Dirty images, upper bounds, preconditioner D and thresholds.
 
     * sigma_MF = Psi^H vect(R)                      eq. mfdimg
+      (Psi = None: the streamed form Re vecdiag(A^H R A))
     * sigma_MVDR = C / (a^H R^{-1} a)               Sec. III-D (unbiased MVDR, K=1)
     * D = (1/(K C)) diag^2(A^H R^{-1} A)            eq. D
     * Var(sigma_MF,i) = (a^H R a)^2 / N             Appendix A (K=1, R -> R_hat)
@@ -155,7 +207,7 @@ def bounds(A: np.ndarray, Psi: np.ndarray, R: np.ndarray, N: int,
     * gamma: the chosen dirty image, optionally inflated (Sec. III-D or
       Appendix A);  eps_i = kappa * std_i of the cost's dirty image (Sec. IV-C)."""
     p = A.shape[0]
-    dirty = dirty_mf(Psi, R)
+    dirty = dirty_mf(Psi, R) if Psi is not None else psi_adjoint(A, R)
     h = mvdr_h(A, R)
     C = bias_constant(N, p, prm.bias_c)
     mv = C / h
@@ -193,20 +245,52 @@ class CostProblem:
           ||W y|| = ||(R^{-T/2} kron R^{-1/2}) y|| for every y because
           W^H W = R^{-T} kron R^{-1}, so cost, gradient and optimum coincide.
     ``to_sigma`` maps the solver variable back to the image (sigma = D^{-1} x)."""
-    M: np.ndarray
+    M: np.ndarray | None
     b: np.ndarray
     upper: np.ndarray
     to_sigma: np.ndarray
+    # streamed form (M is None): M = (conj(B) o B) diag(dinv), B = T A
+    B: np.ndarray | None = None
+    dinv: np.ndarray | None = None
+
+    @property
+    def Q(self) -> int:
+        return self.M.shape[1] if self.M is not None else self.B.shape[1]
+
+    def cols(self, S: np.ndarray):
+        """M[:, S]: a matrix in the explicit form, a KhatriRaoCols otherwise."""
+        if self.M is not None:
+            return self.M[:, S]
+        return KhatriRaoCols(self.B[:, S], self.dinv[S])
+
+    def apply(self, S: np.ndarray, xS: np.ndarray) -> np.ndarray:
+        """M[:, S] @ x_S."""
+        if self.M is not None:
+            return self.M[:, S] @ xS
+        return KhatriRaoCols(self.B[:, S], self.dinv[S]).matvec(xS)
+
+    def adjoint(self, r: np.ndarray) -> np.ndarray:
+        """Re(M^H r) over every pixel."""
+        if self.M is not None:
+            return np.real(self.M.conj().T @ r)
+        return KhatriRaoCols(self.B, self.dinv).rmatvec(r)
 
 
-def cost_problem(A: np.ndarray, Psi: np.ndarray, R: np.ndarray, bnd: Bounds,
+def cost_problem(A: np.ndarray, Psi: np.ndarray | None, R: np.ndarray, bnd: Bounds,
                  cost: int) -> CostProblem:
+    """Psi = None selects the streamed form (Psi and M never stored)."""
     p = R.shape[0]
     if cost == COST_LS:
+        if Psi is None:
+            return CostProblem(None, vect(R).astype(np.complex128), bnd.gamma.copy(),
+                               np.ones_like(bnd.gamma), B=A, dinv=np.ones_like(bnd.gamma))
         return CostProblem(Psi, vect(R).astype(np.complex128), bnd.gamma.copy(),
                            np.ones_like(bnd.gamma))
     Lc = cholesky_lower(R)
     Linv = sla.solve_triangular(Lc, np.eye(p, dtype=np.complex128), lower=True)
+    if Psi is None:
+        return CostProblem(None, vect(Linv @ R @ Linv.conj().T), bnd.D * bnd.gamma, 1.0 / bnd.D,
+                           B=Linv @ A, dinv=1.0 / bnd.D)
     # W Psi = (conj(L^-1) kron L^-1)(conj(A) o A) = conj(L^-1 A) o (L^-1 A): the
     # mixed-product rule for Khatri-Rao products (notation section).  The
     # explicit Kronecker route is checked against this one in the tests.
@@ -219,8 +303,12 @@ def gradient(prob: CostProblem, x: np.ndarray) -> np.ndarray:
     """g(x) = -M^H (b - M x), eq. gWLS specialised in eq. gls / eq. gmvdr
     (K = 1).  M^H of a vectorised Hermitian matrix is real; the real part is
     taken explicitly."""
-    r = prob.b - prob.M @ x
-    return -np.real(prob.M.conj().T @ r)
+    if prob.M is not None:
+        r = prob.b - prob.M @ x
+        return -np.real(prob.M.conj().T @ r)
+    S = np.nonzero(x)[0]                 # M x = M_S x_S: the other terms are zero
+    r = prob.b - prob.apply(S, x[S])
+    return -prob.adjoint(r)
 
 
 # ---------------------------------------------------------------- Sec. V-A
@@ -233,9 +321,18 @@ class LsqrResult:
     arnorm: float
 
 
-def lsqr(M: np.ndarray, b: np.ndarray, atol: float, btol: float,
+def _mv(M, v):
+    return M @ v if isinstance(M, np.ndarray) else M.matvec(v)
+
+
+def _rmv(M, u):
+    return np.real(M.conj().T @ u) if isinstance(M, np.ndarray) else M.rmatvec(u)
+
+
+def lsqr(M, b: np.ndarray, atol: float, btol: float,
          maxit: int) -> LsqrResult:
     """LSQR for min ||b - M x|| over REAL x with complex M and b.
+    M is a matrix or an operator with matvec / rmatvec (KhatriRaoCols).
 
     The u-space is C^{p^2} with the real inner product Re<.,.>; since b and
     every M v are vectorised Hermitian matrices, M^H u is real and the real
@@ -255,7 +352,7 @@ def lsqr(M: np.ndarray, b: np.ndarray, atol: float, btol: float,
     if beta == 0.0:
         return LsqrResult(x, 0, 0, 0.0, 0.0)
     u = b / beta
-    v = np.real(M.conj().T @ u)
+    v = _rmv(M, u)
     alpha = float(np.linalg.norm(v))
     if alpha == 0.0:
         return LsqrResult(x, 0, 2, beta, 0.0)
@@ -267,12 +364,12 @@ def lsqr(M: np.ndarray, b: np.ndarray, atol: float, btol: float,
     istop, it = 3, 0
     for it in range(1, maxit + 1):
         # Golub-Kahan step, eq. lanczos
-        u = M @ v - alpha * u
+        u = _mv(M, v) - alpha * u
         beta = float(np.linalg.norm(u))
         if beta > 0.0:
             u = u / beta
         anorm2 += alpha * alpha + beta * beta
-        v = np.real(M.conj().T @ u) - beta * v
+        v = _rmv(M, u) - beta * v
         alpha = float(np.linalg.norm(v))
         if alpha > 0.0:
             v = v / alpha
@@ -313,7 +410,7 @@ class SolveResult:
 
 
 def active_set(prob: CostProblem, eps: np.ndarray, prm: Params,
-               record: bool = True) -> SolveResult:
+               record: bool = True, progress=None) -> SolveResult:
     """Active-set method of Table I for min 1/2||b - Mx||^2, 0 <= x <= upper.
 
     Start x = 0, all pixels in L, F empty, flag Freegradient-isnotzero = True.
@@ -334,9 +431,10 @@ def active_set(prob: CostProblem, eps: np.ndarray, prm: Params,
     subproblem sits exactly on its bound: one free pixel gives z_i = h_i / C
     against u_i = D_i gamma_i = h_i for PWLS with the MVDR bound (C = 1), and
     z_i = gamma_i for CLS with the MF bound, so the untoleranced test is
-    decided by rounding."""
-    M, b, up = prob.M, prob.b, prob.upper
-    Q = M.shape[1]
+    decided by rounding.  progress(outer, n_free, lsqr_total), when given, is
+    called after every pass (reporting only)."""
+    b, up = prob.b, prob.upper
+    Q = prob.Q
     x = np.zeros(Q)
     sets = np.full(Q, SET_L, dtype=np.int8)
     flag = True
@@ -353,9 +451,9 @@ def active_set(prob: CostProblem, eps: np.ndarray, prm: Params,
             F = np.nonzero(sets == SET_F)[0]
             U = np.nonzero(sets == SET_U)[0]
             if F.size:
-                b_sub = b - M[:, U] @ x[U]
+                b_sub = b - prob.apply(U, x[U])
                 maxit = prm.lsqr_maxit if prm.lsqr_maxit > 0 else 4 * F.size + 20
-                res = lsqr(M[:, F], b_sub, prm.lsqr_atol, prm.lsqr_btol, maxit)
+                res = lsqr(prob.cols(F), b_sub, prm.lsqr_atol, prm.lsqr_btol, maxit)
                 lsqr_total += res.iters
                 z = res.x
             else:
@@ -398,6 +496,8 @@ def active_set(prob: CostProblem, eps: np.ndarray, prm: Params,
             if record:
                 events.append(("free", i_min))
             flag = True
+        if progress is not None:
+            progress(outer, int(np.count_nonzero(sets == SET_F)), lsqr_total)
     return SolveResult(prob.to_sigma * x, x, sets, outer, lsqr_total, converged,
                        events, g)
 
@@ -409,18 +509,20 @@ class ImageResult:
     solve: SolveResult
 
 
-def image(ant_xyz, l, m, lam, R, N, prm: Params) -> ImageResult:
-    """Full pipeline for one job: bounds, then the bounded LS solve."""
+def image(ant_xyz, l, m, lam, R, N, prm: Params, streamed: bool = False,
+          progress=None) -> ImageResult:
+    """Full pipeline for one job: bounds, then the bounded LS solve.
+    streamed: never form Psi (the operator is applied through A)."""
     A = steering_matrix(ant_xyz, l, m, lam)
-    Psi = khatri_rao_psi(A)
+    Psi = None if streamed else khatri_rao_psi(A)
     bnd = bounds(A, Psi, R, N, prm)
     prob = cost_problem(A, Psi, R, bnd, prm.cost)
-    res = active_set(prob, bnd.eps, prm)
+    res = active_set(prob, bnd.eps, prm, progress=progress)
     return ImageResult(bnd, res)
 
 
-def image_job(job, prm: Params) -> ImageResult:
-    return image(job.ant_xyz, job.l, job.m, job.lam, job.R, job.N, prm)
+def image_job(job, prm: Params, streamed: bool = False, progress=None) -> ImageResult:
+    return image(job.ant_xyz, job.l, job.m, job.lam, job.R, job.N, prm, streamed, progress)
 
 
 # ---------------------------------------------------------------- replay
@@ -449,8 +551,8 @@ def active_set_follow(prob: CostProblem, eps: np.ndarray, prm: Params, log, tol:
     Test infrastructure for path-dependent results (kappa > 0): when all
     decisions are admissible, the logged run followed a valid path of the
     method and its image must match the oracle's image along that path."""
-    M, b, up = prob.M, prob.b, prob.upper
-    Q = M.shape[1]
+    b, up = prob.b, prob.upper
+    Q = prob.Q
     x = np.zeros(Q)
     sets = np.full(Q, SET_L, dtype=np.int8)
     rep = FollowReport(result=None)
@@ -470,9 +572,9 @@ def active_set_follow(prob: CostProblem, eps: np.ndarray, prm: Params, log, tol:
             F = np.nonzero(sets == SET_F)[0]
             U = np.nonzero(sets == SET_U)[0]
             if F.size:
-                b_sub = b - M[:, U] @ x[U]
+                b_sub = b - prob.apply(U, x[U])
                 maxit = prm.lsqr_maxit if prm.lsqr_maxit > 0 else 4 * F.size + 20
-                res = lsqr(M[:, F], b_sub, prm.lsqr_atol, prm.lsqr_btol, maxit)
+                res = lsqr(prob.cols(F), b_sub, prm.lsqr_atol, prm.lsqr_btol, maxit)
                 lsqr_total += res.iters
                 z = res.x
             else:

@@ -38,6 +38,15 @@ RECORDS = {
                                prm=O.Params(cost=O.COST_PWLS, kappa=6.0, eps_floor=1e-6, feas_tol=1e-5)),
     "snapshots_extended_bounds": dict(maker=lambda: synth.snapshots_extended(),
                                       prm=O.Params(cost=O.COST_PWLS), bounds_only=True),
+    # 256x256 grid, p = 288 in six clusters within 200 wavelengths, 50 points
+    # + 3 Gaussian blobs, N = 1e4, SNR 0 dB: PWLS with the MVDR bound,
+    # kappa = 6, by the streamed oracle (the explicit Psi would hold 87 GB).
+    # "large_pwls_t" stops after the first 400 passes of Table I (max_outer)
+    "large_pwls": dict(maker=lambda: synth.large(), streamed=True,
+                       prm=O.Params(cost=O.COST_PWLS, kappa=6.0, eps_floor=1e-6, feas_tol=1e-5)),
+    "large_pwls_t": dict(maker=lambda: synth.large(), streamed=True,
+                         prm=O.Params(cost=O.COST_PWLS, kappa=6.0, eps_floor=1e-6, feas_tol=1e-5,
+                                      max_outer=400)),
 }
 
 
@@ -55,7 +64,18 @@ def make(name: str) -> str:
                             N=job.N, bias_c=prm.bias_c, dirty=bnd.dirty, mvdr=bnd.mvdr, assc=bnd.assc,
                             oracle_seconds=time.time() - t0)
         return out
-    res = S.image_snapshot_job(job, prm) if snap else O.image_job(job, prm)
+    if snap:
+        res = S.image_snapshot_job(job, prm)
+    else:
+        last = [time.time()]
+
+        def progress(outer, nf, its):
+            if time.time() - last[0] > 60:
+                last[0] = time.time()
+                print(f"{name}: pass {outer}, |F| {nf}, LSQR iterations {its}, "
+                      f"{time.time() - t0:.0f} s", flush=True)
+
+        res = O.image_job(job, prm, streamed=rec.get("streamed", False), progress=progress)
     dt = time.time() - t0
     extra = dict(assc=res.bounds.assc, K=job.K) if snap else {}
     np.savez_compressed(
@@ -63,7 +83,7 @@ def make(name: str) -> str:
         cost=prm.cost, kappa=prm.kappa, eps_floor=prm.eps_floor, feas_tol=prm.feas_tol,
         dirty=res.bounds.dirty, mvdr=res.bounds.mvdr, gamma=res.bounds.gamma,
         sigma=res.solve.sigma, sets=res.solve.sets, outer=res.solve.outer,
-        lsqr_iters=res.solve.lsqr_iters, converged=res.solve.converged,
+        lsqr_iters=res.solve.lsqr_iters, converged=res.solve.converged, max_outer=prm.max_outer,
         events=np.array([(0 if e[0] == "free" else 1, e[1], e[2] if len(e) > 2 else -1)
                          for e in res.solve.events], dtype=np.int64),
         oracle_seconds=dt)
