@@ -42,6 +42,8 @@ struct img_ctx {
     float *fwd_part = nullptr;   // partial Gram blocks of the wide forward (allocated on first use)
     void *ls_mem = nullptr;      // full-image LSQR vectors (allocated on first use)
     cudaGraphExec_t ls_exec = nullptr;   // one LSQR iteration as a CUDA graph (own stream only)
+    img::WsHost *ws = nullptr;   // graph-driven wide solver (created on the first wide solve)
+    cudaEvent_t ev = nullptr;    // ordering event for batched wide solves
 };
 
 namespace {
@@ -146,6 +148,23 @@ int mode_of(const img_ctx *c) {
 // img_psi / img_psi_adj use the pipelined streamed kernels at every p.
 int op_mode_of(const img_ctx *c) {
     return (c->prm.precision != IMG_PREC_FP32 && c->prm.p <= img::kMaxWideP) ? c->prm.precision : 0;
+}
+
+// Arithmetic of the graph-driven wide solver (64 < p <= 384, tensor cores),
+// or 0 when the job takes the one-CTA solver.
+int wide_of(const img_ctx *c) {
+    return (c->prm.precision != IMG_PREC_FP32 && c->prm.p > img::kMaxTcP && c->prm.p <= img::kMaxWideSolveP)
+               ? c->prm.precision
+               : 0;
+}
+
+// The wide solver's buffers and graph, made on the first wide solve of a
+// context (the graph holds the context's device pointers, which never move).
+img_status wide_ready(img_ctx *c) {
+    if (c->ws) return IMG_OK;
+    const cudaError_t e = img::ws_create(c->hj, c->dj, wide_of(c), &c->ws);
+    if (e == cudaErrorMemoryAllocation) return IMG_ENOMEM;
+    return e == cudaSuccess ? IMG_OK : IMG_ECUDA;
 }
 
 bool finite_all(const double *v, size_t n) {
@@ -446,7 +465,13 @@ img_status img_solve(img_ctx *c, double *sigma, img_solve_info *info, int on_dev
     if (!c || !sigma) return IMG_EINVAL;
     img_status st = prepare(c);
     if (st != IMG_OK) return st;
-    CK(img::launch_solve(c->djp, 1, c->prm.p, mode_of(c), nullptr, nullptr, c->stream));
+    if (wide_of(c)) {
+        st = wide_ready(c);
+        if (st != IMG_OK) return st;
+        CK(img::ws_launch(c->ws, c->stream));
+    } else {
+        CK(img::launch_solve(c->djp, 1, c->prm.p, mode_of(c), nullptr, nullptr, c->stream));
+    }
     DevInfo d{};
     CK(cudaMemcpyAsync(&d, c->hj.info, sizeof(DevInfo), cudaMemcpyDeviceToHost, c->stream));
     st = copy_out_double(c, c->hj.sigma, sigma, c->hj.Q, on_device);
@@ -951,16 +976,56 @@ img_status img_solve_batch(img_ctx *const *ctxs, int n, double *const *sigma, im
         st = launch_prepare(g, s, nullptr);
         if (st != IMG_OK) return st;
     }
+    // wide jobs (64 < p <= 384 on tensor cores) run their solve graphs, each
+    // on its context's stream after the batch's factor and bounds; the other
+    // jobs run the one-CTA solver, one launch per arithmetic group
+    std::vector<int> wide;
+    for (int j = 0; j < n; ++j)
+        if (wide_of(ctxs[j])) {
+            st = wide_ready(ctxs[j]);
+            if (st != IMG_OK) return st;
+            wide.push_back(j);
+        }
+    if (!wide.empty()) {
+        cudaEvent_t ready = nullptr;
+        CK(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+        CK(cudaEventRecord(ready, s));
+        for (int j : wide) {
+            img_ctx *c = ctxs[j];
+            if (!c->ev) CK(cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming));
+            CK(cudaStreamWaitEvent(c->stream, ready, 0));
+            CK(img::ws_launch(c->ws, c->stream));
+            CK(cudaEventRecord(c->ev, c->stream));
+        }
+        CK(cudaEventDestroy(ready));
+    }
     if (on_device)
         CK(cudaMemcpyAsync(g_ws.sig, outs.data(), n * sizeof(double *), cudaMemcpyHostToDevice, s));
     for (int m = 0; m < kGroups; ++m) {
-        const int nb = g.end[m] - g.begin[m];
-        if (!nb) continue;
-        CK(img::launch_solve(g_ws.jobs + g.begin[m], nb, g.max_p[m], Groups::solve_mode(m), g_ws.infos + g.begin[m],
-                             on_device ? g_ws.sig + g.begin[m] : nullptr, s));
+        std::vector<int> idx;               // positions q of this group's one-CTA jobs
+        for (int q = g.begin[m]; q < g.end[m]; ++q)
+            if (!wide_of(ctxs[g.order[q]])) idx.push_back(q);
+        if (idx.empty()) continue;
+        const bool contiguous = (int)idx.size() == g.end[m] - g.begin[m];
+        if (contiguous) {
+            CK(img::launch_solve(g_ws.jobs + g.begin[m], (int)idx.size(), g.max_p[m], Groups::solve_mode(m),
+                                 g_ws.infos + g.begin[m], on_device ? g_ws.sig + g.begin[m] : nullptr, s));
+        } else {
+            for (int q : idx)
+                CK(img::launch_solve(g_ws.jobs + q, 1, ctxs[g.order[q]]->prm.p, Groups::solve_mode(m), g_ws.infos + q,
+                                     on_device ? g_ws.sig + q : nullptr, s));
+        }
     }
+    for (int j : wide) CK(cudaStreamWaitEvent(s, ctxs[j]->ev, 0));
     std::vector<DevInfo> d(n);
     CK(cudaMemcpyAsync(d.data(), g_ws.infos, n * sizeof(DevInfo), cudaMemcpyDeviceToHost, s));
+    std::vector<DevInfo> dw(wide.size());
+    for (size_t k = 0; k < wide.size(); ++k) {
+        img_ctx *c = ctxs[wide[k]];
+        CK(cudaMemcpyAsync(&dw[k], c->hj.info, sizeof(DevInfo), cudaMemcpyDeviceToHost, s));
+        if (on_device)
+            CK(cudaMemcpyAsync(sigma[wide[k]], c->hj.sigma, c->hj.Q * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
     if (!on_device)
         for (int j = 0; j < n; ++j)
             CK(cudaMemcpyAsync(sigma[j], ctxs[j]->hj.sigma, ctxs[j]->hj.Q * sizeof(double),
@@ -969,6 +1034,7 @@ img_status img_solve_batch(img_ctx *const *ctxs, int n, double *const *sigma, im
     img_status first = IMG_OK;
     std::vector<DevInfo> byjob(n);
     for (int q = 0; q < n; ++q) byjob[g.order[q]] = d[q];
+    for (size_t k = 0; k < wide.size(); ++k) byjob[wide[k]] = dw[k];
     for (int j = 0; j < n; ++j) {
         ctxs[j]->prepared = true;
         ctxs[j]->prep_status = byjob[j].status == IMG_ENOTPD ? IMG_ENOTPD : IMG_OK;
@@ -986,6 +1052,8 @@ void img_destroy(img_ctx *c) {
     if (c->fwd_part) cudaFree(c->fwd_part);
     if (c->ls_exec) cudaGraphExecDestroy(c->ls_exec);
     if (c->ls_mem) cudaFree(c->ls_mem);
+    if (c->ws) img::ws_destroy(c->ws);
+    if (c->ev) cudaEventDestroy(c->ev);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -1155,10 +1223,18 @@ struct img_server {
             const size_t pp8 = (size_t)p.p * p.p * sizeof(float2);
             probe.nparts = std::max(1, std::min(2 * std::max(1, sms), (int)std::max<size_t>(1, (4u << 20) / pp8)));
         }
-        const size_t need = carve(&probe, nullptr);
+        probe.hj.p = p.p;
+        probe.hj.Q = p.n_l * p.n_m;
+        probe.hj.cost = p.cost;
+        const size_t need = carve(&probe, nullptr) + (wide_of(&probe) ? img::ws_size(probe.hj) : 0);
         if (bytes_used + need > prm.hbm_budget_bytes) return nullptr;
         img_ctx *c = nullptr;
         if (img_create(&p, &c) != IMG_OK) return nullptr;
+        if (wide_of(c) && wide_ready(c) != IMG_OK) {
+            img_destroy(c);
+            return nullptr;
+        }
+        c->dbytes += wide_of(c) ? img::ws_size(c->hj) : 0;
         bytes_used += c->dbytes;
         all_ctx.push_back(c);
         return c;
@@ -1192,23 +1268,54 @@ struct img_server {
         for (int q = 0; q < n; ++q) ptrs[q] = ctxs[g.order[q]]->dj;
         CK(cudaMemcpyAsync(sl.jobs, sl.stage(ptrs.data(), n * sizeof(JobDev *)), n * sizeof(JobDev *),
                            cudaMemcpyHostToDevice, sl.s));
-        for (int md = 0; md < kGroups; ++md) {
-            const int nb = g.end[md] - g.begin[md];
-            if (!nb) continue;
-            JobDev *const *jp = sl.jobs + g.begin[md];
+        // jobs [q0, q0 + nb) of group md on the one-CTA solver
+        auto launch_range = [&](int md, int q0, int nb, int max_p, int max_tiles) -> img_status {
+            JobDev *const *jp = sl.jobs + q0;
             if (md <= 2) {
                 // one fused kernel: tables, factor, bounds and solve in one CTA per job
-                CK(img::launch_job(jp, nb, g.max_p[md], md, sl.infos + g.begin[md], nullptr, sl.s));
+                CK(img::launch_job(jp, nb, max_p, md, sl.infos + q0, nullptr, sl.s));
             } else {
-                // wide arrays: bounds on the streamed tensor-core operator, as the
-                // single-job API computes them, then the solver
                 CK(img::launch_tables(jp, nb, sl.s));
                 CK(img::launch_factor(jp, nb, sl.s));
-                CK(img::launch_bounds(jp, nb, g.max_tiles[md], g.max_p[md], Groups::bounds_mode(md), sl.s));
+                CK(img::launch_bounds(jp, nb, max_tiles, max_p, Groups::bounds_mode(md), sl.s));
                 CK(img::launch_finalize(jp, nb, sl.s, nullptr));
-                CK(img::launch_solve(jp, nb, g.max_p[md], Groups::solve_mode(md), sl.infos + g.begin[md], nullptr,
-                                     sl.s));
+                CK(img::launch_solve(jp, nb, max_p, Groups::solve_mode(md), sl.infos + q0, nullptr, sl.s));
             }
+            return IMG_OK;
+        };
+        for (int md = 0; md < kGroups; ++md) {
+            std::vector<int> narrow;
+            for (int q = g.begin[md]; q < g.end[md]; ++q) {
+                img_ctx *c = ctxs[g.order[q]];
+                if (!wide_of(c)) {
+                    narrow.push_back(q);
+                    continue;
+                }
+                // wide arrays on tensor cores: tables, factor and bounds (streamed
+                // operator up to p = 256), then the job's solve graph
+                JobDev *const *jp = sl.jobs + q;
+                const int tiles = (c->hj.Q + img::kTile - 1) / img::kTile;
+                CK(img::launch_tables(jp, 1, sl.s));
+                CK(img::launch_factor(jp, 1, sl.s));
+                CK(img::launch_bounds(jp, 1, tiles, c->prm.p, op_mode_of(c), sl.s));
+                CK(img::launch_finalize(jp, 1, sl.s, nullptr));
+                img_status wst = wide_ready(c);
+                if (wst != IMG_OK) return wst;
+                CK(img::ws_launch(c->ws, sl.s));
+                CK(cudaMemcpyAsync(sl.infos + q, c->hj.info, sizeof(DevInfo), cudaMemcpyDeviceToDevice, sl.s));
+            }
+            if (narrow.empty()) continue;
+            img_status rst = IMG_OK;
+            if ((int)narrow.size() == g.end[md] - g.begin[md]) {
+                rst = launch_range(md, g.begin[md], (int)narrow.size(), g.max_p[md], g.max_tiles[md]);
+            } else {
+                for (int q : narrow) {
+                    img_ctx *c = ctxs[g.order[q]];
+                    rst = launch_range(md, q, 1, c->prm.p, (c->hj.Q + img::kTile - 1) / img::kTile);
+                    if (rst != IMG_OK) break;
+                }
+            }
+            if (rst != IMG_OK) return rst;
         }
         CK(cudaMemcpyAsync(sl.h_infos, sl.infos, n * sizeof(DevInfo), cudaMemcpyDeviceToHost, sl.s));
         // results in group order: remember the permutation

@@ -178,9 +178,20 @@ cudaError_t launch_to_double(const float *src, double *dst, int n, cudaStream_t 
 cudaError_t launch_snapshot_image(const SnapPtrs &sp, int K, int Q, int kind, double C, double *out,
                                   cudaStream_t st);
 
+// Wide tensor-core solver (64 < p <= 384, mode 1 or 2): the whole Table I
+// loop of one job as a CUDA graph with device-side conditional nodes.
+// ws_create allocates its buffers and instantiates the graph for the job's
+// device arrays; ws_launch queues one solve on a stream.
+struct WsHost;
+cudaError_t ws_create(const JobDev &hj, const JobDev *dj, int mode, WsHost **out);
+cudaError_t ws_launch(WsHost *w, cudaStream_t st);
+size_t ws_size(const JobDev &hj);         // device bytes ws_create allocates
+void ws_destroy(WsHost *w);
+
 size_t solve_smem_bytes(int p, int mode);
 constexpr int kMaxTcP = 64;   // tensor-core solver: 2p x 2p operand tiles in shared memory
 constexpr int kMaxWideP = 256; // streamed tensor-core operators (bounds, Psi^H)
+constexpr int kMaxWideSolveP = 384;  // graph-driven tensor-core solver above kMaxTcP
 size_t bounds_smem_bytes(int p);
 
 }  // namespace img
