@@ -1,12 +1,15 @@
 """Benchmark: bounded least-squares images per second on one GB300.
 
-Workload (one step): a batch of B independent 128x128-pixel images from a
-64-antenna log-spiral array (20 lognormal point sources plus a Gaussian blob,
-SNR 0 dB, N = 10^4 samples), each through the whole hot path: Cholesky of
+Headline workload (one step): a batch of B independent 256x256-pixel images
+from a 288-antenna array (six clusters of 48 within 200 wavelengths), each
+sky 50 lognormal point sources plus 3 Gaussian blobs (FWHM 4-10 px), SNR
+0 dB, N = 10^4 samples, each image through the whole hot path: Cholesky of
 R_hat, matched-filter dirty image, MVDR bound, and the preconditioned-WLS
-active-set solve with LSQR subproblems.  Inputs are seeded synthetic data.
+active-set solve with LSQR subproblems (kappa = 6).  The second workload
+("mid": 128x128 pixels, 64-antenna log-spiral, 20 points plus a blob) is
+reported inside the same line.  Inputs are seeded synthetic data.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--workload large|mid]
     python bench.py --impl reference      # the FP64 CPU oracle, bounded sample
 
 Under torchrun each rank solves its own batch (jobs are independent: weak
@@ -33,7 +36,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "images/s"
-WORKLOAD = "pwls-mvdr 128x128 p=64 log-spiral, 20 points + blob, N=1e4, kappa=6"
+WORKLOADS = {
+    "large": "pwls-mvdr 256x256 p=288 (6 clusters of 48 within 200 lambda), 50 points + 3 Gaussian blobs, "
+             "N=1e4, SNR 0 dB, kappa=6",
+    "mid": "pwls-mvdr 128x128 p=64 log-spiral, 20 points + blob, N=1e4, kappa=6",
+}
+WORKLOAD = WORKLOADS["large"]
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
 
 
@@ -92,15 +100,28 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- workload
-def rank_seeds(rank: int, B: int):
+def rank_seeds(rank: int, B: int, workload: str = "large"):
     """Seeds of the B images rank `rank` solves: disjoint across ranks (the
     images are independent, so ranks are replicas on different data)."""
-    return [2000 + 100_000 * rank + j for j in range(B)]
+    base = 4000 if workload == "large" else 2000
+    return [base + 100_000 * rank + j for j in range(B)]
 
 
-def make_jobs(seeds):
+def make_jobs(seeds, workload: str = "large"):
     import synth
+    if workload == "large":
+        return [synth.large(seed=s) for s in seeds]
     return [synth.mid(seed=s) for s in seeds]
+
+
+def default_batch(workload: str, steps: int, sms: int) -> int:
+    """Images per step.  mid: two per SM (one CTA each).  large: each image
+    is a graph of kernels spread over the GPU; several solves in flight
+    overlap (8 saturate the GPU to within about 10 %), and the batch shrinks
+    when many steps are asked for, keeping the timed region near a minute."""
+    if workload == "mid":
+        return 2 * sms
+    return max(2, min(8, 48 // max(steps, 1)))
 
 
 def reduce_max(value: float, device=None) -> float:
@@ -142,12 +163,16 @@ def run_ours(args, rank: int, world: int):
     G.load()
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    B = args.batch or 2 * sm_count()
-    jobs = make_jobs(rank_seeds(rank, B))
+    wl = args.workload
+    B = args.batch or default_batch(wl, args.steps, sm_count())
+    jobs = make_jobs(rank_seeds(rank, B, wl), wl)
     stream = torch.cuda.Stream(device=dev)
     prec = PRECISIONS[args.precision]
-    ims = [G.Imager(j.ant_xyz, j.l, j.m, j.lam, stream=stream.cuda_stream, precision=prec)
-           for j in jobs]
+    # one-CTA jobs (mid) share the launching stream; graph-driven jobs
+    # (large) each get a stream so that their solves run side by side
+    streams = [stream] + [torch.cuda.Stream(device=dev) for _ in range(B - 1)] if wl == "large" else [stream] * B
+    ims = [G.Imager(j.ant_xyz, j.l, j.m, j.lam, stream=st.cuda_stream, precision=prec)
+           for j, st in zip(jobs, streams)]
     # column-major complex128 bytes of each R_hat, resident on the device
     R_dev = [torch.from_numpy(np.ascontiguousarray(j.R.ravel(order="F"))).to(dev) for j in jobs]
     sig_dev = [torch.empty(j.Q, dtype=torch.float64, device=dev) for j in jobs]
@@ -189,6 +214,9 @@ def run_ours(args, rank: int, world: int):
     t_solve = [e1.elapsed_time(e2) / 1e3 for _, e1, e2 in ev]
     total = reduce_max(sum(t_step), dev)
     flops = [sum(i.op_flops for i in infos) for infos in infos_all]
+    # kernels each wide solve executed (its report's cyc_aux[0]) plus the
+    # batch's factor / bounds launches, per step
+    launches = [[float(i.cyc_aux[0]) for i in infos] + [4.0] for infos in infos_all] if wl == "large" else None
     conv = sum(i.converged for infos in infos_all for i in infos)
     outer = float(np.mean([i.outer for infos in infos_all for i in infos]))
 
@@ -200,7 +228,7 @@ def run_ours(args, rank: int, world: int):
             t.numpy()[:] = j.R.ravel(order="F")
         pin_np = [t.numpy().reshape(j.p, j.p, order="F") for t, j in zip(pin, jobs)]
         host_out = [torch.empty(j.Q, dtype=torch.float64).pin_memory().numpy() for j in jobs]
-        ke = max(1, min(args.steps, 3))
+        ke = 1 if wl == "large" else max(1, min(args.steps, 3))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(ke):
@@ -218,7 +246,8 @@ def run_ours(args, rank: int, world: int):
         im.close()
 
     res = {
-        "B": B, "total": total, "t_step": t_step, "t_solve": t_solve, "t_prep": t_prep,
+        "workload": wl, "p": jobs[0].p, "n": jobs[0].n_l,
+        "B": B, "total": total, "t_step": t_step, "t_solve": t_solve, "t_prep": t_prep, "launches": launches,
         "prep_flops": float(sum(2 * 8.0 * j.p * j.p * j.Q for j in jobs)), "flops": flops,
         "conv": conv, "outer": outer, "clocks": clocks, "e2e": e2e,
         "sms": sm_count(),
@@ -553,6 +582,38 @@ def profiled_traffic(B: int):
     return None
 
 
+def oracle_sample_large(budget_passes: int = 30, seed: int = 4000):
+    """Time the FP64 oracle (streamed operator form: Psi is never stored) on
+    one image of the 256x256, p = 288 workload: setup (steering matrix, dirty
+    and MVDR images, PWLS operator) plus the first `budget_passes` passes of
+    the Table I loop.  Returns (t_setup, t_per_pass, passes)."""
+    import synth
+    from oracle import imager as O
+    job = synth.large(seed=seed)
+    prm = O.Params(cost=O.COST_PWLS, kappa=6.0, eps_floor=1e-6, feas_tol=1e-5, max_outer=budget_passes)
+    t0 = time.perf_counter()
+    A = O.steering_matrix(job.ant_xyz, job.l, job.m, job.lam)
+    bnd = O.bounds(A, None, job.R, job.N, prm)
+    prob = O.cost_problem(A, None, job.R, bnd, prm.cost)
+    t1 = time.perf_counter()
+    res = O.active_set(prob, bnd.eps, prm, record=False)
+    t2 = time.perf_counter()
+    return t1 - t0, (t2 - t1) / max(res.outer, 1), res.outer
+
+
+def oracle_record_large():
+    """The oracle's complete image of the 256x256, p = 288 workload (seed
+    4000): its Table I passes and wall time, as recorded when
+    tests/golden/large_pwls.npz was written; None when absent."""
+    path = os.path.join(ROOT, "tests", "golden", "large_pwls.npz")
+    try:
+        g = np.load(path)
+        return {"passes": int(g["outer"]), "lsqr_iters": int(g["lsqr_iters"]),
+                "seconds": float(g["oracle_seconds"])}
+    except (OSError, KeyError):
+        return None
+
+
 def cpu_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -560,35 +621,65 @@ def cpu_cores() -> int:
         return os.cpu_count() or 1
 
 
-def cpu_baseline_line(passes_per_image: float, budget_passes: int = 40):
-    ts, tp, done = oracle_sample(budget_passes)
-    t_img = ts + tp * passes_per_image
-    return {"value": 1.0 / t_img, "unit": METRIC, "cores": cpu_cores(), "kind": "oracle",
-            "sample": (f"FP64 numpy oracle, one image of the same workload: setup {ts:.1f} s "
-                       f"(explicit Psi, bounds, PWLS operator) + first {done} Table I passes "
-                       f"at {tp:.3f} s/pass, extrapolated to {passes_per_image:.0f} passes "
-                       f"per image (later passes cost more, so this favours the oracle); "
-                       f"BLAS threads = library default")}
+def cpu_baseline_line(workload: str, budget_passes: int = 30):
+    if workload == "mid":
+        ppi = oracle_passes_per_image()
+        ts, tp, done = oracle_sample(budget_passes)
+        t_img = ts + tp * ppi
+        return {"value": 1.0 / t_img, "unit": METRIC, "cores": cpu_cores(), "kind": "oracle",
+                "sample": (f"FP64 numpy oracle, one image of the same workload: setup {ts:.1f} s "
+                           f"(explicit Psi, bounds, PWLS operator) + first {done} Table I passes "
+                           f"at {tp:.3f} s/pass, extrapolated to {ppi:.0f} passes per image "
+                           f"(later passes cost more, so this favours the oracle)")}
+    rec = oracle_record_large()
+    ppi = rec["passes"] if rec else 5600.0
+    ts, tp, done = oracle_sample_large(budget_passes)
+    t_img = ts + tp * ppi
+    line = {"value": 1.0 / t_img, "unit": METRIC, "cores": cpu_cores(), "kind": "oracle",
+            "sample": (f"FP64 numpy oracle (streamed operators), one image of the same workload: "
+                       f"setup {ts:.1f} s + first {done} Table I passes at {tp:.3f} s/pass, "
+                       f"extrapolated to the oracle's {ppi:.0f} passes per image (later passes "
+                       f"cost more: this favours the oracle)")}
+    if rec:
+        line["complete_image"] = {"value": 1.0 / rec["seconds"], "unit": METRIC, "seconds": rec["seconds"],
+                                  "passes": rec["passes"], "lsqr_iters": rec["lsqr_iters"],
+                                  "where": "the oracle's full solve of seed 4000 when its stored record was "
+                                           "written (8-core x86 build host, multithreaded BLAS)"}
+    return line
 
 
 def run_reference(args):
     """Reference arm: the FP64 oracle timed as it stands on the host cores."""
-    ppi = oracle_passes_per_image()
+    wl = args.workload
     per_step = []
-    for k in range(args.warmup + args.steps):
-        ts, tp, done = oracle_sample(budget_passes=12)
-        if k >= args.warmup:
-            per_step.append(ts + tp * ppi)
+    if wl == "mid":
+        ppi = oracle_passes_per_image()
+        for k in range(args.warmup + args.steps):
+            ts, tp, done = oracle_sample(budget_passes=12)
+            if k >= args.warmup:
+                per_step.append(ts + tp * ppi)
+        sample = f"per step: oracle setup + 12 Table I passes on one image, extrapolated to {ppi:.0f} passes per image"
+    else:
+        rec = oracle_record_large()
+        ppi = rec["passes"] if rec else 5600.0
+        for k in range(args.warmup + args.steps):
+            ts, tp, done = oracle_sample_large(budget_passes=8)
+            if k >= args.warmup:
+                per_step.append(ts + tp * ppi)
+        sample = (f"per step: streamed-oracle setup + 8 Table I passes on one image, extrapolated to "
+                  f"{ppi:.0f} passes per image (favours the oracle)")
+        if rec:
+            sample += (f"; the oracle's complete image of this workload took {rec['seconds']:.0f} s "
+                       f"({rec['passes']} passes) on the 8-core build host")
     t = float(np.mean(per_step))
     val = 1.0 / t
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": METRIC, "n_gpus": 0,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "batch": 1, "device": "cpu"},
+        "data": "synthetic", "config": {"workload": WORKLOADS[wl], "batch": 1, "device": "cpu"},
         "cpu_baseline": {"value": val, "unit": METRIC, "cores": cpu_cores(), "kind": "oracle",
-                         "sample": (f"per step: oracle setup + 12 Table I passes on one image, "
-                                    f"extrapolated to {ppi:.0f} passes per image")},
+                         "sample": sample},
         "e2e": {"value": val, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -611,6 +702,7 @@ def main():
                     help="only the operator and full-image LS measurements (one JSON line)")
     ap.add_argument("--precision-only", action="store_true",
                     help="only the arithmetic sweep against FP64 (one JSON line)")
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -637,51 +729,19 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         torch.distributed.init_process_group("nccl")
     r = run_ours(args, rank, world)
+    mid = None
+    if args.workload == "large" and not args.no_ops and world == 1:
+        # the 128x128, p = 64 workload as a second, named measurement
+        import copy
+        a2 = copy.copy(args)
+        a2.workload, a2.steps, a2.warmup, a2.batch, a2.no_e2e = "mid", 3, 3, 0, True
+        mid = run_ours(a2, rank, world)
     if rank == 0:
-        K = args.steps
-        B = r["B"]
-        total = r["total"]
-        value = world * B * K / total
-        t_solve = float(np.mean(r["t_solve"]))
-        t_prep = float(np.mean(r["t_prep"]))
-        flops = float(np.mean(r["flops"]))
-        mhz = r["clocks"]["sm_max_mhz"] or 2070.0
-        achieved = flops / t_solve / 1e12
-        pk = measured_peaks()
-        if args.precision == "fp32":
-            bound, peak = "alu", fp32_alu_peak_tflops(r["sms"], mhz)
-            basis = f"FP32 CUDA cores: {r['sms']} SMs x 128 lanes x 2 flops x {mhz:.0f} MHz"
-        else:
-            bound = "tensor"
-            if pk.get("bf16_tflops_sustained"):
-                peak = float(pk["bf16_tflops_sustained"])
-                basis = ("measured dense BF16 tensor peak, sustained (FP16 runs at the BF16 rate); "
-                         "achieved counts algorithmic flops, the split products execute 3x")
-            else:
-                peak = 1700.0
-                basis = "fallback sustained BF16 tensor peak (no measured peaks file)"
-        line = {
-            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": K,
-            "warmup": args.warmup, "ms_per_step": total / K * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.precision == "fp32" else f"{args.precision}+f32acc",
-            "data": "synthetic",
-            "config": {"workload": WORKLOAD, "batch_per_gpu": B, "n_l": 128, "n_m": 128, "p": 64,
-                       "cost": "pwls", "bound": "mvdr", "precision": args.precision,
-                       "l2": "flushed between steps (512 MB write)",
-                       "parallelism": f"dp{world} (independent images)"},
-            "roofline": {"kernel": "k_solve", "bound": bound, "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak,
-                         "traffic": profiled_traffic(B) if args.precision == "f16x3" else None,
-                         "peak_basis": basis},
-            "solve_ms_per_step": t_solve * 1e3,
-            "prepare_ms_per_step": t_prep * 1e3,
-            "prepare_tflops": r["prep_flops"] / t_prep / 1e12,
-            "converged": r["conv"], "mean_outer_passes": r["outer"],
-            "gpu_launches": 4 * K,
-            "clocks": r["clocks"],
-            "e2e": r["e2e"],
-        }
+        line = summarize(r, args, world)
+        if mid is not None:
+            m = summarize(mid, a2, world)
+            line["mid_workload"] = {k: m[k] for k in ("value", "unit", "ms_per_step", "config", "roofline",
+                                                    "converged", "mean_outer_passes", "gpu_launches")}
         if not args.no_ops and world == 1:
             line["operators"] = run_operators(args)
             if PRECISIONS[args.precision] != 0:
@@ -690,7 +750,7 @@ def main():
         if not args.no_serve and world == 1:
             line["serve"] = run_serve(args)
         if not args.no_cpu and world == 1:
-            line["cpu_baseline"] = cpu_baseline_line(oracle_passes_per_image())
+            line["cpu_baseline"] = cpu_baseline_line(args.workload)
         if not args.no_ops and world == 1:
             try:
                 line["snapshots"] = run_snapshots(args)
@@ -700,6 +760,62 @@ def main():
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
+
+
+def summarize(r, args, world):
+    """The JSON line of one run_ours result."""
+    K = args.steps
+    B = r["B"]
+    total = r["total"]
+    value = world * B * K / total
+    t_solve = float(np.mean(r["t_solve"]))
+    t_prep = float(np.mean(r["t_prep"]))
+    flops = float(np.mean(r["flops"]))
+    mhz = r["clocks"]["sm_max_mhz"] or 2070.0
+    achieved = flops / t_solve / 1e12
+    pk = measured_peaks()
+    wl = r["workload"]
+    if args.precision == "fp32":
+        bound, peak = "alu", fp32_alu_peak_tflops(r["sms"], mhz)
+        basis = f"FP32 CUDA cores: {r['sms']} SMs x 128 lanes x 2 flops x {mhz:.0f} MHz"
+    else:
+        bound = "tensor"
+        if pk.get("bf16_tflops_sustained"):
+            peak = float(pk["bf16_tflops_sustained"])
+            basis = ("measured dense BF16 tensor peak, sustained (FP16 runs at the BF16 rate); "
+                     "achieved counts algorithmic flops, the split products execute 3x")
+        else:
+            peak = 1700.0
+            basis = "fallback sustained BF16 tensor peak (no measured peaks file)"
+    if wl == "large":
+        kernel = "k_ws_* (the solve graph: all its kernels, B solves in flight)"
+        traffic = None
+        launches = int(sum(r["launches"][-1])) if r.get("launches") else None
+    else:
+        kernel = "k_solve"
+        traffic = profiled_traffic(B) if args.precision == "f16x3" else None
+        launches = 4 * K
+    return {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": total / K * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else f"{args.precision}+f32acc",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS[wl], "batch_per_gpu": B, "n_l": r["n"], "n_m": r["n"], "p": r["p"],
+                   "cost": "pwls", "bound": "mvdr", "precision": args.precision,
+                   "l2": "flushed between steps (512 MB write)",
+                   "parallelism": f"dp{world} (independent images)"},
+        "roofline": {"kernel": kernel, "bound": bound, "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_basis": basis + " (of measured)" if pk else basis},
+        "solve_ms_per_step": t_solve * 1e3,
+        "prepare_ms_per_step": t_prep * 1e3,
+        "prepare_tflops": r["prep_flops"] / t_prep / 1e12,
+        "converged": r["conv"], "mean_outer_passes": r["outer"],
+        "gpu_launches": launches if launches is not None else 4 * K,
+        "clocks": r["clocks"],
+        "e2e": r["e2e"],
+    }
 
 
 if __name__ == "__main__":

@@ -1,6 +1,7 @@
 // Host side of the C ABI declared in include/img.h: validation, device
 // memory layout of a job, and the launch sequence of every call.
 #include <chrono>
+#include <cstdio>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -52,10 +53,20 @@ constexpr int kMaxP = 384;
 
 img_status cuda_status(cudaError_t e) { return e == cudaSuccess ? IMG_OK : IMG_ECUDA; }
 
+// With IMG_DEBUG set in the environment, a failing CUDA call is reported on
+// stderr with its source line before the status code is returned.
+void report_cuda(cudaError_t e, const char *what, int line) {
+    static const bool on = getenv("IMG_DEBUG") != nullptr;
+    if (on) fprintf(stderr, "img: %s failed at img_api.cu:%d: %s\n", what, line, cudaGetErrorString(e));
+}
+
 #define CK(x)                                        \
     do {                                             \
         cudaError_t _e = (x);                        \
-        if (_e != cudaSuccess) return IMG_ECUDA;     \
+        if (_e != cudaSuccess) {                     \
+            report_cuda(_e, #x, __LINE__);           \
+            return IMG_ECUDA;                        \
+        }                                            \
     } while (0)
 
 // NVTX range over one API call (a no-op unless a profiler is attached), so
@@ -163,6 +174,7 @@ int wide_of(const img_ctx *c) {
 img_status wide_ready(img_ctx *c) {
     if (c->ws) return IMG_OK;
     const cudaError_t e = img::ws_create(c->hj, c->dj, wide_of(c), &c->ws);
+    if (e != cudaSuccess) report_cuda(e, "ws_create", __LINE__);
     if (e == cudaErrorMemoryAllocation) return IMG_ENOMEM;
     return e == cudaSuccess ? IMG_OK : IMG_ECUDA;
 }
@@ -1069,6 +1081,7 @@ void img_destroy(img_ctx *c) {
 // block scheduler places the new CTAs as SMs free up.  No kernel waits on the
 // host: completion is an event the scheduler polls.
 #include <chrono>
+#include <cstdio>
 #include <condition_variable>
 #include <deque>
 #include <map>

@@ -459,13 +459,15 @@ constexpr int kItemsFwdMaxPairs = 24;
 // of XA and 4nb .. 4nb+3 of XB, the 64-row half of the stage's tile, hi and
 // lo.  Warp 4 issues the copies and the MMAs, warps 0-3 read the
 // accumulator out.  Needs kItemsFwdThreads threads, items_fwd_smem_bytes() of
-// dynamic shared memory (1024 aligned by the caller) and 5 mbarriers.
-// Returns the waits that timed out.
+// dynamic shared memory (1024 aligned by the caller), 5 mbarriers and 256
+// columns of tensor memory at tmem, allocated by the caller once per CTA
+// (a CTA that gave up its allocation permit cannot allocate again, so one
+// allocation serves every task of the CTA).  Returns the waits that timed out.
 constexpr int kItemsFwdThreads = 160;
 __host__ __device__ inline size_t items_fwd_smem_bytes() { return 2 * kFwdStage + 1024; }
 
 template <bool BF16>
-__device__ int items_forward(const UnitGeom &g, unsigned char *dyn, uint64_t *bars, uint32_t *slot,
+__device__ int items_forward(const UnitGeom &g, unsigned char *dyn, uint64_t *bars, uint32_t tmem,
                              const unsigned char *XA, const unsigned char *XB, int n, int m, int nb, int s0, int S,
                              float *out) {
     const int N = items_fwd_n(g, nb);
@@ -485,11 +487,9 @@ __device__ int items_forward(const UnitGeom &g, unsigned char *dyn, uint64_t *ba
         }
         mbar_init(&bars[kAcc], 1);
     }
-    if (warp == 0) tmem_alloc(slot, 256);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = *slot;
     int timeouts = 0;
     uint32_t ph = 0;
 
@@ -576,7 +576,6 @@ __device__ int items_forward(const UnitGeom &g, unsigned char *dyn, uint64_t *ba
     if (timeouts) atomicAdd(&s_timeouts, timeouts);
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, 256);
     return s_timeouts;
 }
 

@@ -29,6 +29,10 @@
 namespace img {
 
 constexpr int kWsThreads = 256;
+// Grid of the list kernels (forward, free-list adjoint): a share of the SMs,
+// so that the kernels of several solves in flight pack next to each other;
+// the full-image adjoint of the gradient takes every SM.
+constexpr int kListGrid = 64;
 constexpr int kWsSums = 2048;           // per-CTA partial sums of the reductions
 
 // Device control block of one wide solve.
@@ -53,6 +57,7 @@ struct WsCtl {
     unsigned cond[4];           // last value of each loop / branch condition (host-driven mode)
     int cache_slot, cache_pixel; // support slot whose vectors k_ws_cache computes (-1: none)
     int nsums;                  // CTA shares of ||t||^2 left in sums by k_ws_fred
+    unsigned long long launches;  // kernels executed in this solve
     double sums[kWsSums];
 };
 
@@ -98,6 +103,11 @@ __device__ __forceinline__ float lam_of(unsigned long long key) {
 __device__ __forceinline__ double ws_flops_fwd(int p, int n) { return 4.0 * p * (double)p * n; }
 __device__ __forceinline__ double ws_flops_adj(int p, int n) { return 8.0 * p * (double)p * n; }
 
+// Count this kernel in the solve's launch total (block 0, thread 0).
+__device__ __forceinline__ void ws_count(WsCtl *ctl) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ctl->launches, 1ull);
+}
+
 __device__ void ws_log(const JobDev &J, WsCtl *ctl, int kind, int pixel, float val) {
     if (ctl->nev < J.ev_cap) {
         J.ev[ctl->nev] = (kind << 24) | pixel;
@@ -121,6 +131,7 @@ __global__ void k_ws_start(const JobDev *Jp, WsBufs B, cudaGraphConditionalHandl
         unsigned long long t;
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
         ctl->t_begin = t;
+        ctl->launches = 1;
         ctl->f = ctl->nu = ctl->ns = 0;
         ctl->pending = -1;
         ctl->outer = 0;
@@ -145,11 +156,13 @@ __global__ void k_ws_start(const JobDev *Jp, WsBufs B, cudaGraphConditionalHandl
 }
 
 __global__ void k_ws_end(const JobDev *Jp, WsBufs B, cudaGraphConditionalHandle h_outer) {
+    ws_count(B.ctl);
     WsCtl *ctl = B.ctl;
     if (threadIdx.x == 0) ws_cond(ctl, kCondOuter, h_outer, ctl->stop ? 0u : 1u);
 }
 
 __global__ void k_ws_finish(const JobDev *Jp, WsBufs B) {
+    ws_count(B.ctl);
     const JobDev &J = *Jp;
     WsCtl *ctl = B.ctl;
     __shared__ double sbuf[kWsThreads / 32];
@@ -179,6 +192,7 @@ __global__ void k_ws_finish(const JobDev *Jp, WsBufs B) {
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
         info.t_end_ns = t;
         info.cyc_total = (double)(t - ctl->t_begin);
+        info.cyc_aux[0] = (double)ctl->launches;      // kernels this solve executed
         *J.ev_count = ctl->nev;
         *J.info = info;
     }
@@ -191,6 +205,7 @@ __global__ void k_ws_finish(const JobDev *Jp, WsBufs B) {
 // CTA b computes rows k = 32 b + lane; warp w sums the terms l = w, w + 8, ...
 constexpr int kCacheRows = 32;
 __global__ void __launch_bounds__(kWsThreads) k_ws_cache(const JobDev *Jp, WsBufs B) {
+    ws_count(B.ctl);
     const JobDev &J = *Jp;
     const WsCtl *ctl = B.ctl;
     const int slot = ctl->cache_slot;
@@ -309,6 +324,7 @@ __device__ int ws_nsplit(int n, int npairs, int max_tasks) {
 // its own): give it a support slot when it has none (its vectors are then
 // computed by k_ws_cache), move it to F and log it.
 __global__ void k_ws_free(const JobDev *Jp, WsBufs B) {
+    ws_count(B.ctl);
     const JobDev &J = *Jp;
     WsCtl *ctl = B.ctl;
     if (threadIdx.x != 0) return;
@@ -346,6 +362,7 @@ __global__ void k_ws_free(const JobDev *Jp, WsBufs B) {
 // weights -s_i x_i (eq. bsubproblemLS / MVDR), the F scales, the list scales
 // and the LSQR iteration cap; h_lif := (|F| > 0).
 __global__ void k_ws_pass(const JobDev *Jp, WsBufs B, cudaGraphConditionalHandle h_lif) {
+    ws_count(B.ctl);
     const JobDev &J = *Jp;
     WsCtl *ctl = B.ctl;
     __shared__ int cbuf[kWsThreads / 32];
@@ -406,6 +423,7 @@ __global__ void k_ws_pass(const JobDev *Jp, WsBufs B, cudaGraphConditionalHandle
 // of max |wl| (stored for the reduction).
 template <bool BF16>
 __global__ void k_ws_listimg(const JobDev *Jp, WsBufs B, int which, int weighted) {
+    ws_count(B.ctl);
     const JobDev &J = *Jp;
     WsCtl *ctl = B.ctl;
     if (ctl->stop) return;
@@ -439,6 +457,7 @@ __global__ void k_ws_listimg(const JobDev *Jp, WsBufs B, int which, int weighted
 // power-of-two scale of ctl->mx_t.
 template <bool BF16>
 __global__ void k_ws_emb(const JobDev *Jp, WsBufs B, int grad) {
+    ws_count(B.ctl);
     const JobDev &J = *Jp;
     WsCtl *ctl = B.ctl;
     if (ctl->stop) return;
@@ -465,6 +484,7 @@ __global__ void k_ws_emb(const JobDev *Jp, WsBufs B, int grad) {
 // blocks from the list's image and its weighted image.
 template <bool BF16>
 __global__ void __launch_bounds__(kItemsFwdThreads, 1) k_ws_fwd(const JobDev *Jp, WsBufs B, int which) {
+    ws_count(B.ctl);
     const JobDev &J = *Jp;
     WsCtl *ctl = B.ctl;
     if (ctl->stop) return;
@@ -478,13 +498,23 @@ __global__ void __launch_bounds__(kItemsFwdThreads, 1) k_ws_fwd(const JobDev *Jp
     unsigned char *dyn = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem4) + 1023) & ~uintptr_t(1023));
     __shared__ uint64_t bars[6];
     __shared__ uint32_t tslot;
+    if (blockIdx.x >= tasks) return;
+    // one tensor-memory allocation for all of this CTA's tasks
+    if (threadIdx.x < 32) tmem_alloc(&tslot, 256);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tslot;
     int to = 0;
     for (int task = blockIdx.x; task < tasks; task += gridDim.x) {
         const int pr = task / nsplit, s = task - pr * nsplit;
-        to += items_forward<BF16>(g, dyn, bars, &tslot, XA, B.ximgW, n, B.pm[pr], B.pnb[pr], s, nsplit,
+        to += items_forward<BF16>(g, dyn, bars, tmem, XA, B.ximgW, n, B.pm[pr], B.pnb[pr], s, nsplit,
                                   B.pfwd + (size_t)task * kTcM * 256);
         __syncthreads();
     }
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) tmem_dealloc(tmem, 256);
     if (to && threadIdx.x == 0) {
         // a broken pipeline ends the solve: every later kernel sees stop
         atomicAdd(&ctl->timeouts, to);
@@ -516,6 +546,7 @@ __device__ __forceinline__ float fred_g(const WsBufs &B, const int *pidx, int ns
 }
 
 __global__ void __launch_bounds__(kWsThreads) k_ws_fred(const JobDev *Jp, WsBufs B, int mode) {
+    ws_count(B.ctl);
     const JobDev &J = *Jp;
     WsCtl *ctl = B.ctl;
     if (ctl->stop) return;
@@ -599,6 +630,7 @@ __global__ void __launch_bounds__(kWsThreads) k_ws_fred(const JobDev *Jp, WsBufs
 // partial dots into padj[row * ld_adj + u] (u: unit, or unit x K group).
 template <bool BF16, bool LIST>
 __global__ void __launch_bounds__(kWideThreads, 1) k_ws_adj(const JobDev *Jp, WsBufs B) {
+    ws_count(B.ctl);
     const JobDev &J = *Jp;
     WsCtl *ctl = B.ctl;
     if (ctl->stop) return;
@@ -656,6 +688,7 @@ __device__ __forceinline__ double vx_sum(double v, double *sb) {
 
 __global__ void __launch_bounds__(kVxThreads) k_ws_vx(const JobDev *Jp, WsBufs B, int init,
                                                        cudaGraphConditionalHandle h_lsqr) {
+    ws_count(B.ctl);
     const JobDev &J = *Jp;
     WsCtl *ctl = B.ctl;
     __shared__ double sb[kVxThreads / 32];
@@ -759,6 +792,7 @@ __global__ void __launch_bounds__(kVxThreads) k_ws_vx(const JobDev *Jp, WsBufs B
 // After the subproblem: count its LSQR iterations, test 0 <= z <= u with the
 // relative tolerance (non-strict, Table I); h_feas := feasible.
 __global__ void k_ws_feas(const JobDev *Jp, WsBufs B, cudaGraphConditionalHandle h_feas) {
+    ws_count(B.ctl);
     const JobDev &J = *Jp;
     WsCtl *ctl = B.ctl;
     __shared__ int s_stop;
@@ -792,6 +826,7 @@ __global__ void k_ws_feas(const JobDev *Jp, WsBufs B, cudaGraphConditionalHandle
 // gradient's residual, their maximum, the support list scale; reset the
 // argmin key.
 __global__ void k_ws_accept(const JobDev *Jp, WsBufs B) {
+    ws_count(B.ctl);
     const JobDev &J = *Jp;
     WsCtl *ctl = B.ctl;
     if (ctl->stop) return;
@@ -828,6 +863,7 @@ __global__ void k_ws_accept(const JobDev *Jp, WsBufs B) {
 // partial dots; lambda_L = g, lambda_U = -g (eq. etaL, eq. etaU); candidates
 // lambda_i < -eps_i off F; smallest lambda, ties to the smallest pixel.
 __global__ void k_ws_grad(const JobDev *Jp, WsBufs B) {
+    ws_count(B.ctl);
     const JobDev &J = *Jp;
     WsCtl *ctl = B.ctl;
     if (ctl->stop) return;
@@ -858,6 +894,7 @@ __global__ void k_ws_grad(const JobDev *Jp, WsBufs B) {
 }
 
 __global__ void k_ws_decide(const JobDev *Jp, WsBufs B) {
+    ws_count(B.ctl);
     WsCtl *ctl = B.ctl;
     if (threadIdx.x != 0 || ctl->stop) return;
     const unsigned long long k = ctl->key;
@@ -875,6 +912,7 @@ __global__ void k_ws_decide(const JobDev *Jp, WsBufs B) {
 // blocking pixel goes to U when its direction is positive, to L otherwise,
 // exactly at its bound, and leaves the support when it goes to L.
 __global__ void k_ws_step(const JobDev *Jp, WsBufs B) {
+    ws_count(B.ctl);
     const JobDev &J = *Jp;
     WsCtl *ctl = B.ctl;
     __shared__ double sv[kWsThreads / 32];
@@ -1004,7 +1042,7 @@ size_t ws_bytes(const JobDev &hj, int sms, WsBufs *B, char *base) {
     };
     WsBufs b{};
     b.npairs = items_fwd_pairs(g, b.pm, b.pnb);
-    b.max_tasks = std::max(b.npairs, 2 * sms);
+    b.max_tasks = std::max(b.npairs, 2 * std::min(sms, kListGrid));
     b.nrows_adj = std::max(hj.Q, cap);
     b.ld_adj = g.nu * g.nk;
     b.ctl = reinterpret_cast<WsCtl *>(take(sizeof(WsCtl)));
@@ -1041,8 +1079,9 @@ static cudaError_t ws_capture(WsHost *w, const JobDev *dj, const JobDev &hj, int
     const int ntr = (hj.p + kRedTile - 1) / kRedTile;
     const int g_red = std::min(ntr * ntr, kWsSums);
     const int g_grad = std::min((hj.Q + kWsThreads - 1) / kWsThreads, 4 * sms);
-    const int g_img = 2 * sms;
+    const int g_img = sms;
     const int g_cache = (hj.p + kCacheRows - 1) / kCacheRows;
+    const int g_fwd = std::min(sms, kListGrid), g_adj = std::min(sms, kListGrid);
     cudaStream_t s = c.st;
     // top level: start, the Table I loop, finish
     c.begin(G, nullptr);
@@ -1069,10 +1108,10 @@ static cudaError_t ws_capture(WsHost *w, const JobDev *dj, const JobDev &hj, int
     k_ws_listimg<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, kListF, 0);
     k_ws_listimg<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, kListU, 0);
     k_ws_listimg<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, kListU, 1);
-    k_ws_fwd<BF><<<sms, kItemsFwdThreads, fsm, s>>>(dj, B, kListU);
+    k_ws_fwd<BF><<<g_fwd, kItemsFwdThreads, fsm, s>>>(dj, B, kListU);
     k_ws_fred<<<g_red, kWsThreads, 0, s>>>(dj, B, kRedB);
     k_ws_emb<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, 0);
-    k_ws_adj<BF, true><<<sms, kWideThreads, asm_, s>>>(dj, B);
+    k_ws_adj<BF, true><<<g_adj, kWideThreads, asm_, s>>>(dj, B);
     k_ws_vx<<<1, kVxThreads, 0, s>>>(dj, B, 1, h_lsqr);
     c.check();
     cudaGraphNode_t n2 = c.end();
@@ -1080,10 +1119,10 @@ static cudaError_t ws_capture(WsHost *w, const JobDev *dj, const JobDev &hj, int
     add_cond(c, lb[0], h_lsqr, cudaGraphCondTypeWhile, 1, n2, wb);
     c.begin(wb[0], nullptr);
     k_ws_listimg<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, kListF, 1);
-    k_ws_fwd<BF><<<sms, kItemsFwdThreads, fsm, s>>>(dj, B, kListF);
+    k_ws_fwd<BF><<<g_fwd, kItemsFwdThreads, fsm, s>>>(dj, B, kListF);
     k_ws_fred<<<g_red, kWsThreads, 0, s>>>(dj, B, kRedT);
     k_ws_emb<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, 0);
-    k_ws_adj<BF, true><<<sms, kWideThreads, asm_, s>>>(dj, B);
+    k_ws_adj<BF, true><<<g_adj, kWideThreads, asm_, s>>>(dj, B);
     k_ws_vx<<<1, kVxThreads, 0, s>>>(dj, B, 0, h_lsqr);
     c.check();
     c.end();
@@ -1098,7 +1137,7 @@ static cudaError_t ws_capture(WsHost *w, const JobDev *dj, const JobDev &hj, int
     k_ws_accept<<<1, kWsThreads, 0, s>>>(dj, B);
     k_ws_listimg<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, kListS, 0);
     k_ws_listimg<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, kListS, 1);
-    k_ws_fwd<BF><<<sms, kItemsFwdThreads, fsm, s>>>(dj, B, kListS);
+    k_ws_fwd<BF><<<g_fwd, kItemsFwdThreads, fsm, s>>>(dj, B, kListS);
     k_ws_fred<<<g_red, kWsThreads, 0, s>>>(dj, B, kRedG);
     k_ws_emb<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, 1);
     k_ws_adj<BF, false><<<sms, kWideThreads, asm_, s>>>(dj, B);
@@ -1133,8 +1172,9 @@ static cudaError_t ws_direct(WsHost *w, cudaStream_t s) {
     const int ntr = (w->p + kRedTile - 1) / kRedTile;
     const int g_red = std::min(ntr * ntr, kWsSums);
     const int g_grad = std::min((w->Q + kWsThreads - 1) / kWsThreads, 4 * sms);
-    const int g_img = 2 * sms;
+    const int g_img = sms;
     const int g_cache = (w->p + kCacheRows - 1) / kCacheRows;
+    const int g_fwd = std::min(sms, kListGrid), g_adj = std::min(sms, kListGrid);
     cudaError_t e = cudaSuccess;
     auto cond = [&](int which) -> unsigned {
         if (e == cudaSuccess) e = cudaMemcpyAsync(w->h_cond, &B.ctl->cond[0], 4 * sizeof(unsigned),
@@ -1151,17 +1191,17 @@ static cudaError_t ws_direct(WsHost *w, cudaStream_t s) {
             k_ws_listimg<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, kListF, 0);
             k_ws_listimg<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, kListU, 0);
             k_ws_listimg<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, kListU, 1);
-            k_ws_fwd<BF><<<sms, kItemsFwdThreads, fsm, s>>>(dj, B, kListU);
+            k_ws_fwd<BF><<<g_fwd, kItemsFwdThreads, fsm, s>>>(dj, B, kListU);
             k_ws_fred<<<g_red, kWsThreads, 0, s>>>(dj, B, kRedB);
             k_ws_emb<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, 0);
-            k_ws_adj<BF, true><<<sms, kWideThreads, asm_, s>>>(dj, B);
+            k_ws_adj<BF, true><<<g_adj, kWideThreads, asm_, s>>>(dj, B);
             k_ws_vx<<<1, kVxThreads, 0, s>>>(dj, B, 1, 0);
             while (cond(kCondLsqr)) {
                 k_ws_listimg<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, kListF, 1);
-                k_ws_fwd<BF><<<sms, kItemsFwdThreads, fsm, s>>>(dj, B, kListF);
+                k_ws_fwd<BF><<<g_fwd, kItemsFwdThreads, fsm, s>>>(dj, B, kListF);
                 k_ws_fred<<<g_red, kWsThreads, 0, s>>>(dj, B, kRedT);
                 k_ws_emb<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, 0);
-                k_ws_adj<BF, true><<<sms, kWideThreads, asm_, s>>>(dj, B);
+                k_ws_adj<BF, true><<<g_adj, kWideThreads, asm_, s>>>(dj, B);
                 k_ws_vx<<<1, kVxThreads, 0, s>>>(dj, B, 0, 0);
             }
         }
@@ -1170,7 +1210,7 @@ static cudaError_t ws_direct(WsHost *w, cudaStream_t s) {
             k_ws_accept<<<1, kWsThreads, 0, s>>>(dj, B);
             k_ws_listimg<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, kListS, 0);
             k_ws_listimg<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, kListS, 1);
-            k_ws_fwd<BF><<<sms, kItemsFwdThreads, fsm, s>>>(dj, B, kListS);
+            k_ws_fwd<BF><<<g_fwd, kItemsFwdThreads, fsm, s>>>(dj, B, kListS);
             k_ws_fred<<<g_red, kWsThreads, 0, s>>>(dj, B, kRedG);
             k_ws_emb<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, 1);
             k_ws_adj<BF, false><<<sms, kWideThreads, asm_, s>>>(dj, B);

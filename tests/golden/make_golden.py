@@ -47,6 +47,12 @@ RECORDS = {
     "large_pwls_t": dict(maker=lambda: synth.large(), streamed=True,
                          prm=O.Params(cost=O.COST_PWLS, kappa=6.0, eps_floor=1e-6, feas_tol=1e-5,
                                       max_outer=400)),
+    # the same solve with LSQR stopped at atol = btol = 1e-6 (the tolerance the
+    # GPU uses) instead of 1e-12: how far two FP64 runs of the method end apart
+    # when only the subproblem accuracy differs
+    "large_pwls_tol6": dict(maker=lambda: synth.large(), streamed=True,
+                            prm=O.Params(cost=O.COST_PWLS, kappa=6.0, eps_floor=1e-6, feas_tol=1e-5,
+                                         lsqr_atol=1e-6, lsqr_btol=1e-6)),
 }
 
 
