@@ -632,9 +632,13 @@ def active_set_follow(prob: CostProblem, eps: np.ndarray, prm: Params, log, tol:
                 mu[pn] = -x[F][pn] / pdir[pn]
                 mu_max = float(np.min(mu))
                 rep.decisions += 1
-                if (nxt[0] == 2) != (pdir[q] > 0) or mu[q] > mu_max * (1 + tol) + 1e-300:
-                    if F[int(np.argmin(mu))] != i:
-                        rep.violations.append(("clamp", k, float(mu[q] / max(mu_max, 1e-300) - 1)))
+                # the blocking pixel goes to U when its direction is positive,
+                # to L otherwise (Table I): the logged set must match the sign
+                if (nxt[0] == 2) != (pdir[q] > 0):
+                    rep.violations.append(("clamp-set", k, float(pdir[q])))
+                # and it must be the pixel with the smallest step, up to a tie
+                if mu[q] > mu_max * (1 + tol) + 1e-300:
+                    rep.violations.append(("clamp", k, float(mu[q] / max(mu_max, 1e-300) - 1)))
                 if F[int(np.argmin(mu))] != i:
                     rep.ties += 1
                 step = float(mu[q])
