@@ -36,6 +36,11 @@
  *   - No C++ exception crosses this boundary; failures are status codes.
  *   - K > 1 snapshots (Sec. II): one context per snapshot, combined by
  *     img_snapshot_image and img_snapshot_ls_image.
+ *   - Environment: IMG_DEBUG (any value) reports a failing CUDA call of the
+ *     host API on stderr with its source line; IMG_SOLVE_GRAPH=0 runs the
+ *     solver's loop for p > 64 from the host instead of inside its CUDA graph
+ *     (the same kernels in the same order, same results), for tools such as
+ *     kernel profilers that cannot look inside graphs with conditional nodes.
  */
 #ifndef IMG_GB300_H
 #define IMG_GB300_H
@@ -62,10 +67,15 @@ enum { IMG_INFLATE_NONE = 0,                           /* gamma = dirty         
        IMG_INFLATE_RATIO = 1,                          /* (1 + alpha) dirty      */
        IMG_INFLATE_STD = 2 };                          /* dirty + alpha std      */
 enum { IMG_C64 = 0, IMG_C128 = 1 };
-/* Arithmetic of the adjoint operator Psi^H (the dominant product).  The
- * split forms run tcgen05 tensor-core MMAs on v = hi + lo 16-bit parts with
- * FP32 accumulation (3 products); they apply when p <= 64 and fall back to
- * FP32 CUDA cores otherwise. */
+/* Arithmetic of the operator products Psi and Psi^H.  The split forms run
+ * tcgen05 tensor-core MMAs on v = hi + lo 16-bit parts with FP32
+ * accumulation (3 products).  The solver uses them at every p <= 384: up to
+ * p = 64 the whole Table I loop of a job runs in one CTA; above that it runs
+ * as one CUDA graph per job (its loop and branches in device-side
+ * conditional nodes) whose kernels spread each product over the GPU.  The
+ * stand-alone operators (img_psi, img_psi_adj and the dirty / MVDR images)
+ * use them up to p = 256 and CUDA cores above.  IMG_PREC_FP32 runs
+ * everything on CUDA cores, the solver in one CTA per job. */
 enum { IMG_PREC_FP32 = 0,       /* FP32 on CUDA cores                        */
        IMG_PREC_F16X3 = 1,      /* split FP16, power-of-two scaled: ~FP32    */
        IMG_PREC_BF16X3 = 2 };   /* split BF16: ~16 significant bits          */
@@ -130,7 +140,9 @@ typedef struct {
     double lambda_min;   /* smallest multiplier at the last gradient         */
     double op_flops;     /* algorithmic operator flops (Psi: 4p^2|S|,
                             Psi^H: 8p^2|S|) spent in this solve              */
-    double cyc_total;    /* SM clock cycles of the solve                     */
+    double cyc_total;    /* SM clock cycles of the solve (p <= 64); for the
+                            graph-driven solver (p > 64) nanoseconds, and
+                            cyc_aux[0] = kernels the solve executed          */
     double cyc_gradient; /* ... of which in full-image gradients             */
     double cyc_lsqr;     /* ... of which in LSQR subproblems                 */
     double cyc_lsqr_fwd; /* ... of which in LSQR's forward products M v      */
@@ -305,9 +317,12 @@ img_status img_solve_batch(img_ctx *const *ctxs, int n, double *const *sigma,
  *   device memory.  Kout: device memory, p x p complex128 column-major.
  *   stream: cudaStream_t or NULL; the call synchronises it before returning.
  * The first call on a device looks up the array's device address (once per
- * device); make that first call before any stream capture.  Every call
- * reuses the same array: calls that overlap on the GPU (other streams or
- * threads) race with each other; serialise them. */
+ * device and CUDA context: after cudaDeviceReset the next call looks it up
+ * again); make that first call before any stream capture.  A launch failure
+ * of this call itself gives IMG_ECUDA; errors left by earlier, unrelated work
+ * are neither reported nor cleared.  Every call reuses the same array: calls
+ * that overlap on the GPU (other streams or threads) race with each other;
+ * serialise them. */
 img_status img_psi_noalloc(int p, int n_l, int n_m, const double *ant_xyz, const double *l,
                            const double *m, double lambda, const double *x, double *Kout,
                            void *stream);

@@ -12,7 +12,10 @@
 // The arithmetic is the CUDA-core FP32 forward of img_psi: pixels are split
 // into contiguous ranges, one CTA per range accumulates its partial p x p
 // matrix, and a second kernel sums the partials in a fixed order in FP64.
+#include <cuda.h>
+
 #include <mutex>
+#include <utility>
 
 #include "../../include/img.h"
 #include "cta_ops.cuh"
@@ -130,25 +133,77 @@ __global__ void k_noalloc_reduce(const float2 *part, int nparts, int pp, double2
     }
 }
 
-// Device address of g_psi_scratch for the current device, looked up once per
-// device with cudaGetSymbolAddress (the host-side name is only a stand-in).
+// Identity of the current CUDA context, or 0 when the driver cannot say.
+// The driver's functions are reached through the runtime's entry-point query,
+// so the library links no driver library.
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
 std::mutex g_mu;
-void *g_addr[128] = {};
+CtxGetCurrentFn g_get_cur = nullptr;
+CtxGetIdFn g_get_id = nullptr;
+bool g_looked = false;
+
+unsigned long long context_id() {
+    {
+        std::lock_guard<std::mutex> lock(g_mu);
+        if (!g_looked) {
+            cudaDriverEntryPointQueryResult q;
+            if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", reinterpret_cast<void **>(&g_get_cur), 12000,
+                                                 cudaEnableDefault, &q) != cudaSuccess ||
+                q != cudaDriverEntryPointSuccess)
+                g_get_cur = nullptr;
+            if (cudaGetDriverEntryPointByVersion("cuCtxGetId", reinterpret_cast<void **>(&g_get_id), 12000,
+                                                 cudaEnableDefault, &q) != cudaSuccess ||
+                q != cudaDriverEntryPointSuccess)
+                g_get_id = nullptr;
+            g_looked = true;
+        }
+    }
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (!g_get_cur || !g_get_id || g_get_cur(&c) != CUDA_SUCCESS || !c || g_get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of g_psi_scratch for the current device (the host-side name
+// is only a stand-in), looked up with cudaGetSymbolAddress once per device
+// and context: cudaDeviceReset ends the context, and the array may sit
+// elsewhere in the next one, so a new context identity triggers a new lookup.
+struct ScratchAddr {
+    unsigned long long ctx = 0;
+    void *ptr = nullptr;
+};
+ScratchAddr g_addr[128];
 
 cudaError_t scratch_address(void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+    const unsigned long long ctx = context_id();
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
+    ScratchAddr &a = g_addr[dev];
+    if (!a.ptr || (ctx != 0 && ctx != a.ctx)) {
         void *ptr = nullptr;
         e = cudaGetSymbolAddress(&ptr, g_psi_scratch);
         if (e != cudaSuccess) return e;
-        g_addr[dev] = ptr;
+        a.ptr = ptr;
+        a.ctx = ctx;
     }
-    *out = g_addr[dev];
+    *out = a.ptr;
     return cudaSuccess;
+}
+
+// One launch whose own status is returned (earlier errors of unrelated work
+// are neither reported nor cleared here).
+template <class... P, class... A>
+cudaError_t launch(void (*k)(P...), unsigned grid, unsigned block, size_t smem, cudaStream_t st, A &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
 }
 
 }  // namespace
@@ -184,11 +239,11 @@ extern "C" img_status img_psi_noalloc(int p, int n_l, int n_m, const double *ant
     per = ((per + kTile - 1) / kTile) * kTile;
     const int used = (Q + per - 1) / per;
     const size_t sm = (size_t)p * kTile * sizeof(float2);
-    k_noalloc_tables<<<16, kThreads, 0, st>>>(J);
-    k_noalloc_partial<<<used, kThreads, sm, st>>>(J, x, part, per);
-    k_noalloc_reduce<<<(p * p + 255) / 256, 256, 0, st>>>(part, used, p * p,
-                                                          reinterpret_cast<double2 *>(Kout));
-    if (cudaGetLastError() != cudaSuccess) return IMG_ECUDA;
+    if (launch(k_noalloc_tables, 16, kThreads, 0, st, J) != cudaSuccess) return IMG_ECUDA;
+    if (launch(k_noalloc_partial, used, kThreads, sm, st, J, x, part, per) != cudaSuccess) return IMG_ECUDA;
+    if (launch(k_noalloc_reduce, (p * p + 255) / 256, 256, 0, st, (const float2 *)part, used, p * p,
+               reinterpret_cast<double2 *>(Kout)) != cudaSuccess)
+        return IMG_ECUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return IMG_ECUDA;
     return IMG_OK;
 }

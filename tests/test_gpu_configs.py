@@ -82,7 +82,7 @@ def _replay_case(G, job, cost, prec):
     Psi = O.khatri_rao_psi(A)
     bnd = O.bounds(A, Psi, job.R, job.N, prm)
     prob = O.cost_problem(A, Psi, job.R, bnd, cost)
-    rep = O.active_set_follow(prob, bnd.eps, prm, log, tol=1e-4)
+    rep = O.active_set_follow(prob, bnd.eps, prm, log, tol=1e-6)
     return sigma, info, rep
 
 
