@@ -534,15 +534,12 @@ __global__ void __launch_bounds__(kItemsFwdThreads, 1) k_ws_fwd(const JobDev *Jp
 // stored below the diagonal transposed on the way.
 constexpr int kRedTile = 32;
 
-// sum over the nsplit partials of the stored Gram entry (r, c), r <= c
-// (blocks are column-major: entry (r, c) of block (m, nb) at (c - 256 nb) 128 + r - 128 m)
-__device__ __forceinline__ float fred_g(const WsBufs &B, const int *pidx, int nsplit, int r, int c) {
+// address of the stored Gram entry (r, c), r <= c, in the first partial of
+// its block (blocks are column-major: entry (r, c) of block (m, nb) at
+// (c - 256 nb) 128 + r - 128 m); partial q follows at q 128 256
+__device__ __forceinline__ const float *fred_at(const WsBufs &B, const int *pidx, int nsplit, int r, int c) {
     const int m = r >> 7, nb = c >> 8;
-    const float *blk = B.pfwd + (size_t)pidx[m * 4 + nb] * nsplit * kTcM * 256 + (size_t)(c - 256 * nb) * kTcM +
-                       (r - 128 * m);
-    float s = 0.f;
-    for (int q = 0; q < nsplit; ++q) s += blk[(size_t)q * kTcM * 256];
-    return s;
+    return B.pfwd + (size_t)pidx[m * 4 + nb] * nsplit * kTcM * 256 + (size_t)(c - 256 * nb) * kTcM + (r - 128 * m);
 }
 
 __global__ void __launch_bounds__(kWsThreads) k_ws_fred(const JobDev *Jp, WsBufs B, int mode) {
@@ -574,21 +571,52 @@ __global__ void __launch_bounds__(kWsThreads) k_ws_fred(const JobDev *Jp, WsBufs
         const int a0 = (tile % nt) * kRedTile, b0 = (tile / nt) * kRedTile;
         if (n > 0) {
             // the stored blocks are column-major: lanes run along the stored
-            // row index (coalesced), i along the column
-            for (int i = ty; i < kRedTile; i += 8) {
+            // row index (coalesced), i along the column.  Each thread gathers
+            // the addresses of all its entries first, then sums the partials
+            // with every load of a partial in flight at once.
+            const float *src[4][6];
+            float acc[4][6];
+#pragma unroll
+            for (int ii = 0; ii < 4; ++ii) {
+                const int i = ty + 8 * ii;
                 const int a = a0 + tx, b = b0 + i;           // element (a, b) = tile [tx][i]
                 const int bt = b0 + tx, at = a0 + i;         // element (at, bt) = tile [i][tx]
-                // G(a, b): stored at (a, b) when a <= b, else at (b, a)
-                if ((a0 < b0 || (a0 == b0 && a <= b)) && a < p && b < p) {
-                    T[0][tx][i] = fred_g(B, pidx, nsplit, a, b);
-                    T[1][tx][i] = fred_g(B, pidx, nsplit, Kp + a, Kp + b);
+                const bool up = (a0 < b0 || (a0 == b0 && a <= b)) && a < p && b < p;
+                const bool lo = (a0 > b0 || (a0 == b0 && bt <= at)) && at < p && bt < p;
+                src[ii][0] = up ? fred_at(B, pidx, nsplit, a, b) : nullptr;              // G(a, b)
+                src[ii][1] = up ? fred_at(B, pidx, nsplit, Kp + a, Kp + b) : nullptr;    // G(Kp+a, Kp+b)
+                src[ii][2] = lo ? fred_at(B, pidx, nsplit, bt, at) : nullptr;            // G(at, bt)
+                src[ii][3] = lo ? fred_at(B, pidx, nsplit, Kp + bt, Kp + at) : nullptr;
+                src[ii][4] = (a < p && b < p) ? fred_at(B, pidx, nsplit, a, Kp + b) : nullptr;     // G(a, Kp+b)
+                src[ii][5] = (at < p && bt < p) ? fred_at(B, pidx, nsplit, bt, Kp + at) : nullptr; // G(b, Kp+a)
+#pragma unroll
+                for (int e = 0; e < 6; ++e) acc[ii][e] = 0.f;
+            }
+            for (int q = 0; q < nsplit; ++q) {
+                const size_t off = (size_t)q * kTcM * 256;
+                float v[4][6];
+#pragma unroll
+                for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+                    for (int e = 0; e < 6; ++e) v[ii][e] = src[ii][e] ? src[ii][e][off] : 0.f;
+#pragma unroll
+                for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+                    for (int e = 0; e < 6; ++e) acc[ii][e] += v[ii][e];
+            }
+#pragma unroll
+            for (int ii = 0; ii < 4; ++ii) {
+                const int i = ty + 8 * ii;
+                if (src[ii][0]) {
+                    T[0][tx][i] = acc[ii][0];
+                    T[1][tx][i] = acc[ii][1];
                 }
-                if ((a0 > b0 || (a0 == b0 && bt <= at)) && at < p && bt < p) {
-                    T[0][i][tx] = fred_g(B, pidx, nsplit, bt, at);
-                    T[1][i][tx] = fred_g(B, pidx, nsplit, Kp + bt, Kp + at);
+                if (src[ii][2]) {
+                    T[0][i][tx] = acc[ii][2];
+                    T[1][i][tx] = acc[ii][3];
                 }
-                if (a < p && b < p) T[2][tx][i] = fred_g(B, pidx, nsplit, a, Kp + b);     // G(a, Kp+b)
-                if (at < p && bt < p) T[3][i][tx] = fred_g(B, pidx, nsplit, bt, Kp + at); // G(b, Kp+a)
+                if (src[ii][4]) T[2][tx][i] = acc[ii][4];
+                if (src[ii][5]) T[3][i][tx] = acc[ii][5];
             }
         }
         __syncthreads();
@@ -709,8 +737,14 @@ __global__ void __launch_bounds__(kVxThreads) k_ws_vx(const JobDev *Jp, WsBufs B
     float ss = 0.f;
     for (int j = threadIdx.x; j < f; j += blockDim.x) {
         float y = 0.f;
-        const float *pr = B.padj + (size_t)j * ld;
-        for (int u = 0; u < rows; ++u) y += pr[u];
+        const float4 *pr = reinterpret_cast<const float4 *>(B.padj + (size_t)j * ld);
+        const int r4 = rows >> 2;
+        float4 s4[9];                                   // rows <= nu nk <= 36
+#pragma unroll
+        for (int q = 0; q < 9; ++q) s4[q] = q < r4 ? pr[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) y += (s4[q].x + s4[q].y) + (s4[q].z + s4[q].w);
+        for (int u = 4 * r4; u < rows; ++u) y += B.padj[(size_t)j * ld + u];
         y *= sc;
         const float vn = init ? J.sF[j] * (y * fus) : J.sF[j] * (y * fus) - fb * J.v[j];
         J.v[j] = vn;
@@ -1044,7 +1078,7 @@ size_t ws_bytes(const JobDev &hj, int sms, WsBufs *B, char *base) {
     b.npairs = items_fwd_pairs(g, b.pm, b.pnb);
     b.max_tasks = std::max(b.npairs, 2 * std::min(sms, kListGrid));
     b.nrows_adj = std::max(hj.Q, cap);
-    b.ld_adj = g.nu * g.nk;
+    b.ld_adj = (g.nu * g.nk + 3) / 4 * 4;    // a multiple of 4: rows read as float4
     b.ctl = reinterpret_cast<WsCtl *>(take(sizeof(WsCtl)));
     b.dvec = hj.cost == IMG_COST_PWLS ? reinterpret_cast<float2 *>(take((size_t)cap * p * sizeof(float2))) : nullptr;
     b.dmax = reinterpret_cast<float *>(take((size_t)cap * sizeof(float)));
