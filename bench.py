@@ -489,22 +489,19 @@ def run_precision(args):
     return out
 
 
-def run_serve(args, rate: float = 200.0, seconds: float = 10.0, distinct: int = 48):
-    """Poisson arrivals of mixed jobs into the continuous-batching server;
-    latencies are the server's submit-to-done times."""
-    import synth
-    import paper_1505_01348_gb300 as G
-    prec = PRECISIONS[args.precision]
-    pool = [synth.serve_job_tc(j) for j in range(distinct)]
-    rng = np.random.default_rng(77)
+def _serve_stream(G, pool, prec, rate, seconds, reserve_wide, reserve_narrow, seed=77):
+    """Poisson arrivals of the pool's jobs (cycled) into the continuous-batching
+    server; latencies are the server's submit-to-done times."""
+    distinct = len(pool)
+    rng = np.random.default_rng(seed)
     n = int(rate * seconds)
     gaps = rng.exponential(1.0 / rate, n)
     srv = G.Server(hbm_budget_bytes=120 << 30)
     shapes = {}
     for j in pool:
         shapes.setdefault((j.p, j.n_l, j.n_m), j)
-    for j in shapes.values():                            # pool contexts before the clock starts
-        srv.reserve(j, 2 * sm_count(), precision=prec)
+    for (p, _, _), j in shapes.items():                 # pool contexts before the clock starts
+        srv.reserve(j, reserve_wide if p > 64 else reserve_narrow, precision=prec)
     ids = []
     t0 = time.perf_counter()
     t_next = t0
@@ -521,22 +518,69 @@ def run_serve(args, rate: float = 200.0, seconds: float = 10.0, distinct: int = 
     t_end = time.perf_counter()
     srv.close()
     lat = np.array(lat)
-    # the plain per-job FP32 path: one job at a time through img_solve
-    sample = pool[:6]
+    return {"rate_jobs_s": rate, "jobs": n, "offered_s": seconds, "images_s": n / (t_end - t0),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "max_ms": float(lat.max())}
+
+
+def run_serve(args, full_rate: float = 3.0, full_seconds: float = 30.0, tc_rate: float = 200.0,
+              tc_seconds: float = 10.0, distinct: int = 48):
+    """Serving under load.  full: the whole job mix (p in {32, 64, 128, 256},
+    grids 64^2 .. 256^2), at the highest Poisson rate measured to keep up
+    (about 3.4 jobs/s served when 4 are offered); tc_subset: the jobs with
+    p <= 64 at 200 jobs/s.  The plain per-job FP32 path (one img_solve at a
+    time) is timed on the p <= 64 subset: on the full mix its p = 256 jobs run
+    the one-CTA CUDA-core solver for hours."""
+    import synth
+    import paper_1505_01348_gb300 as G
+    prec = PRECISIONS[args.precision]
+    full_pool = [synth.serve_job(j) for j in range(distinct)]
+    full = _serve_stream(G, full_pool, prec, full_rate, full_seconds, 16, 64)
+    full["mix"] = (f"{distinct} distinct seeded jobs cycled: p in {{32,64,128,256}}, 64^2, 128^2 or 256^2 grid, "
+                   "5-50 sources, N=1e4; arrivals Poisson; 200 jobs/s is beyond one GPU for this mix")
+    tc_pool = [synth.serve_job_tc(j) for j in range(distinct)]
+    tc = _serve_stream(G, tc_pool, prec, tc_rate, tc_seconds, 16, 2 * sm_count())
+    tc["mix"] = f"{distinct} distinct seeded jobs cycled: p in {{32,64}}, 64^2 or 128^2 grid, 5-50 sources"
+    sample = tc_pool[:6]
     t1 = time.perf_counter()
     for job in sample:
         im = G.Imager.from_job(job, precision=0)
         im.solve()
         im.close()
     per_job = len(sample) / (time.perf_counter() - t1)
-    return {"rate_jobs_s": rate, "jobs": n, "offered_s": seconds,
-            "images_s": n / (t_end - t0), "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()),
-            "mix": f"{distinct} distinct seeded jobs cycled: p in {{32,64}}, 64^2 or 128^2 grid, "
-                   "5-50 sources, N=1e4; arrivals Poisson",
-            "precision": args.precision,
+    return {"precision": args.precision, "full_mix": full, "tc_subset": tc,
             "per_job_fp32_images_s": per_job,
-            "per_job_fp32_sample": f"{len(sample)} jobs of the mix, one img_solve at a time"}
+            "per_job_fp32_sample": f"{len(sample)} jobs of the p <= 64 subset, one img_solve at a time"}
+
+
+def run_batch(args, channels: int = 64):
+    """The uneven 64-channel batch (p in {48, 64, 96}, grids 64^2 .. 128^2,
+    wavelength 1 .. 1.5): factor and bounds in one launch per arithmetic
+    group, the p <= 64 channels in one solver launch (a CTA each), the p = 96
+    channels as solve graphs side by side on their own streams; timed per
+    arithmetic after a warm call."""
+    import torch
+    import synth
+    import paper_1505_01348_gb300 as G
+    jobs = [synth.batch_channel(c) for c in range(channels)]
+    out = {"channels": channels, "p_counts": {str(p): sum(1 for j in jobs if j.p == p) for p in (48, 64, 96)}}
+    for name, prec in (("fp32", 0), ("f16x3", 1), ("bf16x3", 2)):
+        streams = [torch.cuda.Stream() for _ in jobs]
+        ims = [G.Imager(j.ant_xyz, j.l, j.m, j.lam, precision=prec, stream=st.cuda_stream)
+               for j, st in zip(jobs, streams)]
+        for rep in range(2):
+            for im, j in zip(ims, jobs):
+                im.set_covariance(j.R, j.N)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            G.prepare_batch(ims)
+            _, infos = G.solve_batch(ims)
+            dt = time.perf_counter() - t0
+        out[name] = {"s_per_batch": dt, "images_s": channels / dt,
+                     "converged": int(sum(i.converged for i in infos))}
+        for im in ims:
+            im.close()
+    return out
 
 
 # ---------------------------------------------------------------- oracle timing
@@ -749,6 +793,8 @@ def main():
             line["precision_sweep"] = run_precision(args)
         if not args.no_serve and world == 1:
             line["serve"] = run_serve(args)
+        if not args.no_ops and world == 1:
+            line["batch_64_channels"] = run_batch(args)
         if not args.no_cpu and world == 1:
             line["cpu_baseline"] = cpu_baseline_line(args.workload)
         if not args.no_ops and world == 1:
