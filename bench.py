@@ -117,11 +117,11 @@ def make_jobs(seeds, workload: str = "large"):
 def default_batch(workload: str, steps: int, sms: int) -> int:
     """Images per step.  mid: two per SM (one CTA each).  large: each image
     is a graph of kernels spread over the GPU; several solves in flight
-    overlap (8 saturate the GPU to within about 10 %), and the batch shrinks
-    when many steps are asked for, keeping the timed region near a minute."""
+    overlap (8 saturate the GPU to within about 10 %); the batch shrinks to 4
+    when many steps are asked for, to keep the timed region short."""
     if workload == "mid":
         return 2 * sms
-    return max(2, min(8, 48 // max(steps, 1)))
+    return max(4, min(8, 96 // max(steps, 1)))
 
 
 def reduce_max(value: float, device=None) -> float:
@@ -361,6 +361,14 @@ def run_ls_images(args, iters: int = 100):
     return out
 
 
+def _steer64(ant, l, m, lam, il, im):
+    """FP64 steering vectors of pixels (il, im), unit norm, -j sign (the data
+    model's definition; host check values, no oracle code)."""
+    n = np.sqrt(np.maximum(0.0, 1.0 - l[il] ** 2 - m[im] ** 2))
+    dirs = np.stack([l[il], m[im], n])
+    return np.exp(-2j * np.pi * (ant @ dirs) / lam) / np.sqrt(ant.shape[0])
+
+
 def run_snapshots(args, iters: int = 100):
     """K > 1 snapshots on the stand-in for the paper's extended-source
     simulation (p = 100 antennas in a disk, K = 2 snapshots with the array
@@ -420,72 +428,50 @@ def run_snapshots(args, iters: int = 100):
     return out
 
 
-def _steer64(ant, l, m, lam, il, im):
-    """FP64 steering vectors of pixels (il, im), unit norm, -j sign (the data
-    model's definition; host check values, no oracle code)."""
-    n = np.sqrt(np.maximum(0.0, 1.0 - l[il] ** 2 - m[im] ** 2))
-    dirs = np.stack([l[il], m[im], n])
-    return np.exp(-2j * np.pi * (ant @ dirs) / lam) / np.sqrt(ant.shape[0])
-
-
 def run_precision(args):
-    """Arithmetic sweep against FP64 (config 4's report on the tensor-core
-    range): operators on the first 256 antennas of the p = 288 clustered
-    array (sub-array covariance R_hat[:256, :256]) on the 256x256 grid,
-    relative L2 errors on 256 sampled pixels (dirty image, MVDR bound) and of
-    Psi x for a 128-pixel sparse x on every 4th grid line, each against FP64
-    sums evaluated here; and
-    the bench image (128x128, p = 64, PWLS) against the stored FP64 oracle
-    record, with its Table I passes and LSQR iterations.  p = 288 itself has
-    only the FP32 path (tensor-core operands up to p = 256)."""
+    """Arithmetic sweep against FP64 on the 256x256, p = 288 workload:
+    relative L2 errors of the dirty and MVDR images (all pixels) against the
+    stored FP64 oracle record, and the first 400 Table I passes of the solve
+    against the oracle's record of the same 400 passes (image error, same
+    final sets, LSQR iterations); then the 128x128, p = 64 image (whole
+    solve) against its stored record."""
     import paper_1505_01348_gb300 as G
-    import synth
-
-    big = synth.large()
-    p = 256
-    ant, R = big.ant_xyz[:p], big.R[:p, :p]
-    rng = np.random.default_rng(11)
-    Q = big.n_l * big.n_m
-    idx = rng.choice(Q, 256, replace=False)
-    As = _steer64(ant, big.l, big.m, big.lam, idx % big.n_l, idx // big.n_l)
-    d_ref = np.real(np.einsum("ki,kl,li->i", As.conj(), R, As))
-    h_ref = np.real(np.einsum("ki,kl,li->i", As.conj(), np.linalg.inv(R), As))
-    # Psi x on every 4th grid line (64x64): the FP32 forward at p = 256 splits
-    # the pixels over few CTAs, so the full grid would take seconds there
-    ls_, ms_ = big.l[::4], big.m[::4]
-    Qs = ls_.shape[0] * ms_.shape[0]
-    xs_idx = rng.choice(Qs, 128, replace=False)
-    xs_val = rng.uniform(0.1, 2.0, 128)
-    Ax = _steer64(ant, ls_, ms_, big.lam, xs_idx % ls_.shape[0], xs_idx // ls_.shape[0])
-    K_ref = (Ax * xs_val[None, :]) @ Ax.conj().T
-    x = np.zeros(Qs)
-    x[xs_idx] = xs_val
     rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    big = np.load(os.path.join(ROOT, "tests", "golden", "large_pwls_t.npz"))
     gold = np.load(os.path.join(ROOT, "tests", "golden", "mid_pwls.npz"))
-    out = {"operators": f"p = {p} (sub-array of the p = 288 clustered array), 256x256 grid",
-           "image": "bench image 128x128, p = 64, PWLS, vs the stored FP64 oracle record",
-           "oracle_outer_passes": int(gold["outer"]), "oracle_lsqr_iters": int(gold["lsqr_iters"])}
-    for name, prec in sorted(PRECISIONS.items(), key=lambda kv: kv[1]):
-        im = G.Imager(ant, big.l, big.m, big.lam, precision=prec)
-        im.set_covariance(R, big.N)
+    out = {"large": ("256x256, p = 288: bounds and the first Table I passes (400; the FP32 arm 100) vs the "
+                     "stored FP64 oracle records of those passes"),
+           "mid": "bench image 128x128, p = 64, PWLS, whole solve vs the stored FP64 oracle record",
+           "mid_oracle_outer_passes": int(gold["outer"]), "mid_oracle_lsqr_iters": int(gold["lsqr_iters"]),
+           "not_built": "TF32x3 and FP64 arithmetic"}
+
+    def solve(rec, prec, max_outer=0):
+        im = G.Imager(rec["ant_xyz"], rec["l"], rec["m"], float(rec["lam"]), cost=int(rec["cost"]),
+                      kappa=float(rec["kappa"]), eps_floor=float(rec["eps_floor"]),
+                      feas_tol=float(rec["feas_tol"]), precision=prec, max_outer=max_outer)
+        im.set_covariance(rec["R"], int(rec["N"]))
         d, mv = im.dirty(), im.mvdr_bound()
-        im.close()
-        im = G.Imager(ant, ls_, ms_, big.lam, precision=prec)
-        im.set_covariance(R, big.N)
-        K = im.psi(x)
-        im.close()
-        imb = G.Imager(gold["ant_xyz"], gold["l"], gold["m"], float(gold["lam"]), cost=int(gold["cost"]),
-                       kappa=float(gold["kappa"]), eps_floor=float(gold["eps_floor"]),
-                       feas_tol=float(gold["feas_tol"]), precision=prec)
-        imb.set_covariance(gold["R"], int(gold["N"]))
         t0 = time.perf_counter()
-        sigma, info = imb.solve()
+        sigma, info = im.solve()
         ts = time.perf_counter() - t0
-        imb.close()
-        out[name] = {"dirty_rel": rel(d[idx], d_ref), "mvdr_rel": rel(mv[idx], 1.0 / h_ref),
-                     "psi_rel": rel(K, K_ref), "image_rel": rel(sigma, gold["sigma"]),
-                     "outer_passes": int(info.outer), "lsqr_iters": int(info.lsqr_iters),
-                     "solve_s": ts}
+        sets = im.sets()
+        im.close()
+        return d, mv, sigma, info, sets, ts
+
+    big100 = np.load(os.path.join(ROOT, "tests", "golden", "large_pwls_t100.npz"))
+    for name, prec in sorted(PRECISIONS.items(), key=lambda kv: kv[1]):
+        # the FP32 arm runs the one-CTA CUDA-core solver: its 100 first passes
+        rec = big100 if prec == 0 else big
+        npass = int(rec["max_outer"])
+        d, mv, sigma, info, sets, ts = solve(rec, prec, npass)
+        _, _, sig2, info2, _, ts2 = solve(gold, prec)
+        out[name] = {"large_dirty_rel": rel(d, big["dirty"]), "large_mvdr_rel": rel(mv, big["mvdr"]),
+                     "large_passes": npass, "large_image_rel": rel(sigma, rec["sigma"]),
+                     "large_sets_equal": bool(np.array_equal(sets, rec["sets"])),
+                     "large_lsqr_iters": int(info.lsqr_iters),
+                     "large_oracle_lsqr_iters": int(rec["lsqr_iters"]), "large_solve_s": ts,
+                     "mid_image_rel": rel(sig2, gold["sigma"]), "mid_outer_passes": int(info2.outer),
+                     "mid_lsqr_iters": int(info2.lsqr_iters), "mid_solve_s": ts2}
     return out
 
 

@@ -179,6 +179,11 @@ img_status wide_ready(img_ctx *c) {
     return e == cudaSuccess ? IMG_OK : IMG_ECUDA;
 }
 
+// Dirty image and MVDR denominators on the work-item tensor-core adjoint of
+// the wide solver (tensor-core jobs with 256 < p <= 384, where the streamed
+// operator of tc_wide.cuh does not reach).
+bool items_bounds(const img_ctx *c) { return wide_of(c) != 0 && c->prm.p > img::kMaxWideP; }
+
 bool finite_all(const double *v, size_t n) {
     for (size_t i = 0; i < n; ++i)
         if (!std::isfinite(v[i])) return false;
@@ -193,8 +198,14 @@ img_status prepare(img_ctx *c) {
     if (!c->has_cov) return IMG_EINVAL;
     if (c->prepared) return (img_status)c->prep_status;
     CK(img::launch_factor(c->djp, 1, c->stream));
-    const int ntiles = (c->hj.Q + img::kTile - 1) / img::kTile;
-    CK(img::launch_bounds(c->djp, 1, ntiles, c->prm.p, op_mode_of(c), c->stream));
+    if (items_bounds(c)) {
+        img_status st = wide_ready(c);
+        if (st != IMG_OK) return st;
+        CK(img::ws_bounds(c->ws, c->hj, c->stream));
+    } else {
+        const int ntiles = (c->hj.Q + img::kTile - 1) / img::kTile;
+        CK(img::launch_bounds(c->djp, 1, ntiles, c->prm.p, op_mode_of(c), c->stream));
+    }
     CK(img::launch_finalize(c->djp, 1, c->stream, nullptr));
     int flag = 0;
     CK(cudaMemcpyAsync(&flag, c->hj.flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -873,16 +884,20 @@ namespace {
 // Keys 0..2: solver and bounds in arithmetic k (FP32, F16X3, BF16X3, the
 // latter two for p <= 64); keys 3, 4: bounds on the streamed tensor-core
 // operator in F16X3 / BF16X3 (64 < p <= 256), solver on CUDA cores.
-constexpr int kGroups = 5;
+// Key 5: tensor-core jobs with 256 < p <= 384, whose bounds run on the
+// work-item adjoint one job at a time (and whose solve is a graph).
+constexpr int kGroups = 6;
+constexpr int kItemsGroup = 5;
 struct Groups {
     std::vector<int> order;
     int begin[kGroups] = {}, end[kGroups] = {};
-    int max_p[kGroups] = {}, max_tiles[kGroups] = {1, 1, 1, 1, 1};
+    int max_p[kGroups] = {}, max_tiles[kGroups] = {1, 1, 1, 1, 1, 1};
     static int solve_mode(int k) { return k <= 2 ? k : 0; }
-    static int bounds_mode(int k) { return k <= 2 ? k : k - 2; }
+    static int bounds_mode(int k) { return k <= 2 ? k : (k <= 4 ? k - 2 : 0); }
 };
 
 int group_key(const img_ctx *c) {
+    if (items_bounds(c)) return kItemsGroup;
     const int m = mode_of(c), om = op_mode_of(c);
     return (m == 0 && om != 0) ? om + 2 : m;
 }
@@ -912,14 +927,24 @@ img_status check_batch(img_ctx *const *ctxs, int n) {
 }
 
 // Factor + bounds of the listed jobs (device pointer array already in
-// g_ws.jobs in group order), one launch per kernel and group.
-img_status launch_prepare(const Groups &g, cudaStream_t s, int *status_out) {
+// g_ws.jobs in group order), one launch per kernel and group; the bounds of
+// the work-item group run job by job.
+img_status launch_prepare(img_ctx *const *ctxs, const Groups &g, cudaStream_t s, int *status_out) {
     for (int m = 0; m < kGroups; ++m) {
         const int nb = g.end[m] - g.begin[m];
         if (!nb) continue;
         JobDev *const *jp = g_ws.jobs + g.begin[m];
         CK(img::launch_factor(jp, nb, s));
-        CK(img::launch_bounds(jp, nb, g.max_tiles[m], g.max_p[m], Groups::bounds_mode(m), s));
+        if (m == kItemsGroup) {
+            for (int q = g.begin[m]; q < g.end[m]; ++q) {
+                img_ctx *c = ctxs[g.order[q]];
+                img_status st = wide_ready(c);
+                if (st != IMG_OK) return st;
+                CK(img::ws_bounds(c->ws, c->hj, s));
+            }
+        } else {
+            CK(img::launch_bounds(jp, nb, g.max_tiles[m], g.max_p[m], Groups::bounds_mode(m), s));
+        }
         CK(img::launch_finalize(jp, nb, s, status_out ? status_out + g.begin[m] : nullptr));
     }
     return IMG_OK;
@@ -943,7 +968,7 @@ img_status img_prepare_batch(img_ctx *const *ctxs, int n) {
     std::vector<JobDev *> ptrs(n);
     for (int q = 0; q < n; ++q) ptrs[q] = ctxs[g.order[q]]->dj;
     CK(cudaMemcpyAsync(g_ws.jobs, ptrs.data(), n * sizeof(JobDev *), cudaMemcpyHostToDevice, s));
-    st = launch_prepare(g, s, g_ws.status);
+    st = launch_prepare(ctxs, g, s, g_ws.status);
     if (st != IMG_OK) return st;
     std::vector<int> flags(n);
     CK(cudaMemcpyAsync(flags.data(), g_ws.status, n * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -985,7 +1010,7 @@ img_status img_solve_batch(img_ctx *const *ctxs, int n, double *const *sigma, im
     CK(cudaMemcpyAsync(g_ws.jobs, ptrs.data(), n * sizeof(JobDev *), cudaMemcpyHostToDevice, s));
     if (need_prep) {
         // prepared jobs are simply recomputed: same inputs, same results
-        st = launch_prepare(g, s, nullptr);
+        st = launch_prepare(ctxs, g, s, nullptr);
         if (st != IMG_OK) return st;
     }
     // wide jobs (64 < p <= 384 on tensor cores) run their solve graphs, each
@@ -1308,12 +1333,13 @@ struct img_server {
                 // operator up to p = 256), then the job's solve graph
                 JobDev *const *jp = sl.jobs + q;
                 const int tiles = (c->hj.Q + img::kTile - 1) / img::kTile;
-                CK(img::launch_tables(jp, 1, sl.s));
-                CK(img::launch_factor(jp, 1, sl.s));
-                CK(img::launch_bounds(jp, 1, tiles, c->prm.p, op_mode_of(c), sl.s));
-                CK(img::launch_finalize(jp, 1, sl.s, nullptr));
                 img_status wst = wide_ready(c);
                 if (wst != IMG_OK) return wst;
+                CK(img::launch_tables(jp, 1, sl.s));
+                CK(img::launch_factor(jp, 1, sl.s));
+                if (items_bounds(c)) CK(img::ws_bounds(c->ws, c->hj, sl.s));
+                else CK(img::launch_bounds(jp, 1, tiles, c->prm.p, op_mode_of(c), sl.s));
+                CK(img::launch_finalize(jp, 1, sl.s, nullptr));
                 CK(img::ws_launch(c->ws, sl.s));
                 CK(cudaMemcpyAsync(sl.infos + q, c->hj.info, sizeof(DevInfo), cudaMemcpyDeviceToDevice, sl.s));
             }

@@ -185,6 +185,9 @@ cudaError_t launch_snapshot_image(const SnapPtrs &sp, int K, int Q, int kind, do
 struct WsHost;
 cudaError_t ws_create(const JobDev &hj, const JobDev *dj, int mode, WsHost **out);
 cudaError_t ws_launch(WsHost *w, cudaStream_t st);
+// Dirty image (hj.dirty) and MVDR denominators (hj.h) of the job on the
+// work-item tensor-core adjoint, after its factor (for 256 < p <= 384).
+cudaError_t ws_bounds(WsHost *w, const JobDev &hj, cudaStream_t st);
 size_t ws_size(const JobDev &hj);         // device bytes ws_create allocates
 void ws_destroy(WsHost *w);
 

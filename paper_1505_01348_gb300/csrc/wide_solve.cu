@@ -456,7 +456,7 @@ __global__ void k_ws_listimg(const JobDev *Jp, WsBufs B, int which, int weighted
 // B unit image of the matrix U (W0 for LSQR, W1 for the gradient) with the
 // power-of-two scale of ctl->mx_t.
 template <bool BF16>
-__global__ void k_ws_emb(const JobDev *Jp, WsBufs B, int grad) {
+__global__ void k_ws_emb(const JobDev *Jp, WsBufs B, int grad, const float2 *Um) {
     ws_count(B.ctl);
     const JobDev &J = *Jp;
     WsCtl *ctl = B.ctl;
@@ -464,7 +464,7 @@ __global__ void k_ws_emb(const JobDev *Jp, WsBufs B, int grad) {
     const UnitGeom g = unit_geom(J.p);
     const float sc = pow2_scale(__uint_as_float(ctl->mx_t)) * kLift;
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl->sB = sc;
-    const float2 *U = grad ? J.W1 : J.W0;
+    const float2 *U = Um ? Um : (grad ? J.W1 : J.W0);
     const int rows = unit_rows(g);
     const long long total = (long long)g.nu * g.nk * rows * 8;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
@@ -992,6 +992,46 @@ __global__ void k_ws_step(const JobDev *Jp, WsBufs B) {
 }
 
 
+// ---------------------------------------------------------------- bounds
+// Dirty image and MVDR denominators (Sec. III-C, III-D) on the work-item
+// adjoint: out_i = Re(a_i^H U a_i) for U = R_hat and U = R_hat^-1 over every
+// pixel, from the unit image of U.  k_ws_bnd_max readies the control block
+// (no solve runs on the context meanwhile) and reduces max |U|;
+// k_ws_bnd_out sums each pixel's unit partial dots.
+__global__ void k_ws_bnd_max(const JobDev *Jp, WsBufs B, const float2 *U, int first) {
+    const JobDev &J = *Jp;
+    WsCtl *ctl = B.ctl;
+    if (first && blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->stop = J.flags[0] != 0 ? 1 : 0;      // a failed factor leaves the bounds alone
+        ctl->timeouts = 0;
+    }
+    const int pp = J.p * J.p;
+    float mx = 0.f;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < pp; e += gridDim.x * blockDim.x)
+        mx = fmaxf(mx, fmaxf(fabsf(U[e].x), fabsf(U[e].y)));
+    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&ctl->mx_t, __float_as_uint(mx));
+}
+
+__global__ void k_ws_bnd_out(const JobDev *Jp, WsBufs B, float *out) {
+    const JobDev &J = *Jp;
+    WsCtl *ctl = B.ctl;
+    if (ctl->timeouts && blockIdx.x == 0 && threadIdx.x == 0) J.flags[2] = IMG_ETIMEOUT;
+    if (ctl->stop) return;
+    const UnitGeom g = unit_geom(J.p);
+    const float sc = 1.f / (steer_scale(J.p) * kLift * ctl->sB);
+    const int ld = B.ld_adj;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < J.Q; i += gridDim.x * blockDim.x) {
+        float y = 0.f;
+        for (int u = 0; u < g.nu; ++u) y += B.padj[(size_t)i * ld + u];
+        out[i] = y * sc;
+    }
+}
+
+__global__ void k_ws_bnd_reset(WsBufs B) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) B.ctl->mx_t = 0u;
+}
+
 // ================================================================ host side
 namespace {
 
@@ -1144,7 +1184,7 @@ static cudaError_t ws_capture(WsHost *w, const JobDev *dj, const JobDev &hj, int
     k_ws_listimg<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, kListU, 1);
     k_ws_fwd<BF><<<g_fwd, kItemsFwdThreads, fsm, s>>>(dj, B, kListU);
     k_ws_fred<<<g_red, kWsThreads, 0, s>>>(dj, B, kRedB);
-    k_ws_emb<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, 0);
+    k_ws_emb<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, 0, nullptr);
     k_ws_adj<BF, true><<<g_adj, kWideThreads, asm_, s>>>(dj, B);
     k_ws_vx<<<1, kVxThreads, 0, s>>>(dj, B, 1, h_lsqr);
     c.check();
@@ -1155,7 +1195,7 @@ static cudaError_t ws_capture(WsHost *w, const JobDev *dj, const JobDev &hj, int
     k_ws_listimg<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, kListF, 1);
     k_ws_fwd<BF><<<g_fwd, kItemsFwdThreads, fsm, s>>>(dj, B, kListF);
     k_ws_fred<<<g_red, kWsThreads, 0, s>>>(dj, B, kRedT);
-    k_ws_emb<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, 0);
+    k_ws_emb<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, 0, nullptr);
     k_ws_adj<BF, true><<<g_adj, kWideThreads, asm_, s>>>(dj, B);
     k_ws_vx<<<1, kVxThreads, 0, s>>>(dj, B, 0, h_lsqr);
     c.check();
@@ -1173,7 +1213,7 @@ static cudaError_t ws_capture(WsHost *w, const JobDev *dj, const JobDev &hj, int
     k_ws_listimg<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, kListS, 1);
     k_ws_fwd<BF><<<g_fwd, kItemsFwdThreads, fsm, s>>>(dj, B, kListS);
     k_ws_fred<<<g_red, kWsThreads, 0, s>>>(dj, B, kRedG);
-    k_ws_emb<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, 1);
+    k_ws_emb<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, 1, nullptr);
     k_ws_adj<BF, false><<<sms, kWideThreads, asm_, s>>>(dj, B);
     k_ws_grad<<<g_grad, kWsThreads, 0, s>>>(dj, B);
     k_ws_decide<<<1, 32, 0, s>>>(dj, B);
@@ -1227,14 +1267,14 @@ static cudaError_t ws_direct(WsHost *w, cudaStream_t s) {
             k_ws_listimg<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, kListU, 1);
             k_ws_fwd<BF><<<g_fwd, kItemsFwdThreads, fsm, s>>>(dj, B, kListU);
             k_ws_fred<<<g_red, kWsThreads, 0, s>>>(dj, B, kRedB);
-            k_ws_emb<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, 0);
+            k_ws_emb<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, 0, nullptr);
             k_ws_adj<BF, true><<<g_adj, kWideThreads, asm_, s>>>(dj, B);
             k_ws_vx<<<1, kVxThreads, 0, s>>>(dj, B, 1, 0);
             while (cond(kCondLsqr)) {
                 k_ws_listimg<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, kListF, 1);
                 k_ws_fwd<BF><<<g_fwd, kItemsFwdThreads, fsm, s>>>(dj, B, kListF);
                 k_ws_fred<<<g_red, kWsThreads, 0, s>>>(dj, B, kRedT);
-                k_ws_emb<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, 0);
+                k_ws_emb<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, 0, nullptr);
                 k_ws_adj<BF, true><<<g_adj, kWideThreads, asm_, s>>>(dj, B);
                 k_ws_vx<<<1, kVxThreads, 0, s>>>(dj, B, 0, 0);
             }
@@ -1246,7 +1286,7 @@ static cudaError_t ws_direct(WsHost *w, cudaStream_t s) {
             k_ws_listimg<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, kListS, 1);
             k_ws_fwd<BF><<<g_fwd, kItemsFwdThreads, fsm, s>>>(dj, B, kListS);
             k_ws_fred<<<g_red, kWsThreads, 0, s>>>(dj, B, kRedG);
-            k_ws_emb<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, 1);
+            k_ws_emb<BF><<<g_img, kWsThreads, 0, s>>>(dj, B, 1, nullptr);
             k_ws_adj<BF, false><<<sms, kWideThreads, asm_, s>>>(dj, B);
             k_ws_grad<<<g_grad, kWsThreads, 0, s>>>(dj, B);
             k_ws_decide<<<1, 32, 0, s>>>(dj, B);
@@ -1309,6 +1349,8 @@ cudaError_t ws_create(const JobDev &hj, const JobDev *dj, int mode, WsHost **out
     char *base = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(w->mem) + 1023) & ~uintptr_t(1023));
     ws_bytes(hj, sms, &w->B, base);
     e = w->bf16 ? ws_carveout<true>() : ws_carveout<false>();
+    if (e == cudaSuccess) e = set_smem(k_ws_adj<true, false>, items_smem_bytes());
+    if (e == cudaSuccess) e = set_smem(k_ws_adj<false, false>, items_smem_bytes());
     if (e != cudaSuccess) {
         ws_destroy(w);
         return e;
@@ -1333,6 +1375,29 @@ cudaError_t ws_create(const JobDev &hj, const JobDev *dj, int mode, WsHost **out
     }
     *out = w;
     return cudaSuccess;
+}
+
+cudaError_t ws_bounds(WsHost *w, const JobDev &hj, cudaStream_t st) {
+    const WsBufs &B = w->B;
+    const JobDev *dj = w->dj;
+    const int sms = w->sms;
+    const size_t asm_ = items_smem_bytes();
+    const int gq = std::min((hj.Q + kWsThreads - 1) / kWsThreads, 4 * sms);
+    for (int k = 0; k < 2; ++k) {
+        const float2 *U = k == 0 ? hj.R32 : hj.Ri32;
+        k_ws_bnd_reset<<<1, 32, 0, st>>>(B);
+        k_ws_bnd_max<<<sms, kWsThreads, 0, st>>>(dj, B, U, k == 0);
+        if (w->bf16) {
+            k_ws_emb<true><<<sms, kWsThreads, 0, st>>>(dj, B, 0, U);
+            k_ws_adj<true, false><<<sms, kWideThreads, asm_, st>>>(dj, B);
+        } else {
+            k_ws_emb<false><<<sms, kWsThreads, 0, st>>>(dj, B, 0, U);
+            k_ws_adj<false, false><<<sms, kWideThreads, asm_, st>>>(dj, B);
+        }
+        k_ws_bnd_out<<<gq, kWsThreads, 0, st>>>(dj, B, k == 0 ? hj.dirty : hj.h);
+    }
+    k_ws_bnd_reset<<<1, 32, 0, st>>>(B);
+    return cudaGetLastError();
 }
 
 cudaError_t ws_launch(WsHost *w, cudaStream_t st) {

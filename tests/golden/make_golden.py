@@ -47,6 +47,11 @@ RECORDS = {
     "large_pwls_t": dict(maker=lambda: synth.large(), streamed=True,
                          prm=O.Params(cost=O.COST_PWLS, kappa=6.0, eps_floor=1e-6, feas_tol=1e-5,
                                       max_outer=400)),
+    # the first 100 passes (the FP32 arm of the arithmetic sweep, whose
+    # one-CTA CUDA-core solver takes minutes for 400 passes at p = 288)
+    "large_pwls_t100": dict(maker=lambda: synth.large(), streamed=True,
+                            prm=O.Params(cost=O.COST_PWLS, kappa=6.0, eps_floor=1e-6, feas_tol=1e-5,
+                                         max_outer=100)),
     # the same solve with LSQR stopped at atol = btol = 1e-6 (the tolerance the
     # GPU uses) instead of 1e-12: how far two FP64 runs of the method end apart
     # when only the subproblem accuracy differs
