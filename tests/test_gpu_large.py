@@ -2,7 +2,11 @@
 wavelengths, 50 point sources and 3 Gaussian blobs, N = 1e4, SNR 0 dB)
 against the stored oracle record of its first 400 Table I passes
 (tests/golden/large_pwls_t.npz, written by tests/golden/make_golden.py with
-the streamed oracle).
+the streamed oracle), and the complete solve against the oracle's complete
+solves: large_pwls_tol6.npz runs LSQR to the GPU's stopping tolerance
+(atol = btol = 1e-6) and must be followed decision for decision;
+large_pwls.npz (1e-12) parts from it at a tie and is compared through the
+stopping conditions of the method.
 
 The GPU runs the same 400 passes (max_outer) on the record's covariance.
 Its dirty and MVDR images must match the oracle's within 1e-5; its decision
@@ -76,7 +80,35 @@ def rec_full():
     return np.load(os.path.join(HERE, "golden", "large_pwls.npz"))
 
 
-def test_large_full_solve_ends_at_a_kkt_point(G, rec_full):
+@pytest.fixture(scope="module")
+def full_solve(G, rec_full):
+    rec = rec_full
+    im = G.Imager(rec["ant_xyz"], rec["l"], rec["m"], float(rec["lam"]), cost=int(rec["cost"]),
+                  kappa=float(rec["kappa"]), eps_floor=float(rec["eps_floor"]), feas_tol=float(rec["feas_tol"]),
+                  precision=1)
+    im.set_covariance(rec["R"], int(rec["N"]))
+    sigma, info = im.solve()
+    sets = im.sets()
+    log = [(k, q) for k, q, _ in im.events()]
+    atol = im.prm.lsqr_atol
+    im.close()
+    return sigma, info, sets, log, atol
+
+
+def test_large_full_solve_follows_the_oracle_at_the_same_lsqr_tolerance(full_solve):
+    """The oracle in FP64 with LSQR stopped at the GPU's tolerance: the same
+    decisions in the same order over the whole solve (about 2800 pixels
+    freed), the same sets, the image within 1e-4."""
+    rec = np.load(os.path.join(HERE, "golden", "large_pwls_tol6.npz"))
+    sigma, info, sets, log, atol = full_solve
+    olog = [(0, int(q)) if k == 0 else ((1 if e2 == O.SET_L else 2), int(q)) for k, q, e2 in rec["events"]]
+    assert log == olog
+    assert info.outer == int(rec["outer"])
+    np.testing.assert_array_equal(sets, rec["sets"])
+    assert _rel(sigma, rec["sigma"]) <= IMG_TOL
+
+
+def test_large_full_solve_ends_at_a_kkt_point(G, rec_full, full_solve):
     """The complete solve (about 5600 passes).  Past a tie within 1e-6 of
     scale the GPU's path and the oracle's differ, and with the detection
     threshold (kappa = 6) the method's result depends on its path, so the
@@ -89,13 +121,7 @@ def test_large_full_solve_ends_at_a_kkt_point(G, rec_full):
     rec = rec_full
     prm = O.Params(cost=int(rec["cost"]), kappa=float(rec["kappa"]), eps_floor=float(rec["eps_floor"]),
                    feas_tol=float(rec["feas_tol"]))
-    im = G.Imager(rec["ant_xyz"], rec["l"], rec["m"], float(rec["lam"]), cost=prm.cost, kappa=prm.kappa,
-                  eps_floor=prm.eps_floor, feas_tol=prm.feas_tol, precision=1)
-    im.set_covariance(rec["R"], int(rec["N"]))
-    sigma, info = im.solve()
-    sets = im.sets()
-    atol = im.prm.lsqr_atol
-    im.close()
+    sigma, info, sets, _, atol = full_solve
     assert info.converged == 1
     A = O.steering_matrix(rec["ant_xyz"], rec["l"], rec["m"], float(rec["lam"]))
     bnd = O.bounds(A, None, rec["R"], int(rec["N"]), prm)
