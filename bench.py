@@ -256,10 +256,24 @@ def run_ours(args, rank: int, world: int):
 
 
 # ---------------------------------------------------------------- serving
-def run_operators(args, cases=((64, 256), (128, 256), (256, 256), (256, 512)), reps: int = 20):
+def unit_kp(p: int) -> int:
+    """Padded feature count of the tensor-core operand: p rounded up to 32,
+    and above p = 256 further up until it splits into at most 8 units of a
+    multiple of 16 rows, each unit at most 128."""
+    kp = (p + 31) // 32 * 32
+    if p <= 256:
+        return kp
+    while not any(kp % nu == 0 and (kp // nu) % 16 == 0 for nu in range((kp + 127) // 128, 9)):
+        kp += 32
+    return kp
+
+
+def run_operators(args, cases=((64, 256), (128, 256), (256, 256), (256, 512), (288, 256)), reps: int = 20):
     """Operator pair img_psi_adj / img_psi on full n x n grids: p = 64, 128
-    and 256 on 256x256 (the serving mix's largest grid) and p = 256 on
-    512x512; both run the streamed, warp-specialised tensor-core kernels.
+    and 256 on 256x256 (the serving mix's largest grid), p = 256 on 512x512
+    and p = 288 on 256x256; up to p = 256 both run the streamed,
+    warp-specialised tensor-core kernels; at p = 288 the adjoint runs the
+    solver's (tile, unit) work-item kernel and the forward CUDA cores.
     Adjoint Psi^H (Eq. 16): the streamed tensor-core kernel; each call reduces
     max |U|, writes the chunked operand image from the complex128 U and runs
     the adjoint; calls are queued back to back on one stream and timed with
@@ -302,8 +316,8 @@ def run_operators(args, cases=((64, 256), (128, 256), (256, 256), (256, 512)), r
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) / 1e3 / reps
         im.close()
-        kp = (p + 31) // 32 * 32
-        tiles = ((n + 7) // 8) * ((n + 15) // 16)
+        kp = unit_kp(p)
+        tiles = ((n + 7) // 8) * ((n + 15) // 16) if p <= 256 else (job.Q + 127) // 128
         useful = 8.0 * p * p * job.Q
         issued = 3 * 2.0 * 128 * (2 * kp) ** 2 * tiles
         rec = {"adjoint_us_per_call": t * 1e6, "adjoint_useful_tflops": useful / t / 1e12,
@@ -322,6 +336,13 @@ def run_operators(args, cases=((64, 256), (128, 256), (256, 256), (256, 512)), r
         torch.cuda.synchronize()
         tf = e0.elapsed_time(e1) / 1e3 / reps
         im2.close()
+        if p > 256:
+            # the forward runs on CUDA cores above p = 256
+            rec.update({"forward_us_per_call": tf * 1e6,
+                        "forward_useful_tflops": 4.0 * p * p * job.Q / tf / 1e12,
+                        "forward_kernel": "CUDA cores (k_psi_partial + k_psi_reduce)"})
+            out_d[f"p{p}_{n}"] = rec
+            continue
         nf = 2 * kp
         blocks = [(m, nb) for m in range((nf + 127) // 128) for nb in range((nf + 255) // 256)
                   if 256 * nb + min(256, nf - 256 * nb) - 1 >= 128 * m]

@@ -586,7 +586,14 @@ img_status img_psi_adj(img_ctx *c, const double *U, double *out, int on_device) 
     CK(cudaMemcpyAsync(c->Z, U, (size_t)p * p * sizeof(double2),
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     CK(img::launch_z2c(c->Z, c->U32, p * p, c->stream));
-    CK(img::launch_psi_adj(c->dj, c->U32, on_device ? out : c->outd, Q, p, op_mode_of(c), c->stream));
+    if (items_bounds(c)) {
+        // 256 < p <= 384 on tensor cores: the solver's work-item adjoint
+        img_status st = wide_ready(c);
+        if (st != IMG_OK) return st;
+        CK(img::ws_psi_adj(c->ws, c->hj, c->U32, on_device ? out : c->outd, c->stream));
+    } else {
+        CK(img::launch_psi_adj(c->dj, c->U32, on_device ? out : c->outd, Q, p, op_mode_of(c), c->stream));
+    }
     if (on_device == 2) return IMG_OK;           // stream-ordered, no host wait
     if (on_device) return sync(c);
     return copy_out_double(c, c->outd, out, Q, 0);

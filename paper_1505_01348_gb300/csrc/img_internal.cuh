@@ -188,6 +188,9 @@ cudaError_t ws_launch(WsHost *w, cudaStream_t st);
 // Dirty image (hj.dirty) and MVDR denominators (hj.h) of the job on the
 // work-item tensor-core adjoint, after its factor (for 256 < p <= 384).
 cudaError_t ws_bounds(WsHost *w, const JobDev &hj, cudaStream_t st);
+// out_i = Re(a_i^H U a_i) for every pixel on the same kernels (U p x p FP32
+// complex on the device, out Q doubles on the device).
+cudaError_t ws_psi_adj(WsHost *w, const JobDev &hj, const float2 *U, double *out, cudaStream_t st);
 size_t ws_size(const JobDev &hj);         // device bytes ws_create allocates
 void ws_destroy(WsHost *w);
 

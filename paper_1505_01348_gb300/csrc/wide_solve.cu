@@ -1002,7 +1002,9 @@ __global__ void k_ws_bnd_max(const JobDev *Jp, WsBufs B, const float2 *U, int fi
     const JobDev &J = *Jp;
     WsCtl *ctl = B.ctl;
     if (first && blockIdx.x == 0 && threadIdx.x == 0) {
-        ctl->stop = J.flags[0] != 0 ? 1 : 0;      // a failed factor leaves the bounds alone
+        // bounds (first = 1): a failed factor leaves them alone; the
+        // stand-alone adjoint (first = 2) does not depend on the factor
+        ctl->stop = first == 1 && J.flags[0] != 0 ? 1 : 0;
         ctl->timeouts = 0;
     }
     const int pp = J.p * J.p;
@@ -1025,6 +1027,20 @@ __global__ void k_ws_bnd_out(const JobDev *Jp, WsBufs B, float *out) {
         float y = 0.f;
         for (int u = 0; u < g.nu; ++u) y += B.padj[(size_t)i * ld + u];
         out[i] = y * sc;
+    }
+}
+
+__global__ void k_ws_adj_out(const JobDev *Jp, WsBufs B, double *out) {
+    const JobDev &J = *Jp;
+    WsCtl *ctl = B.ctl;
+    if (ctl->stop) return;
+    const UnitGeom g = unit_geom(J.p);
+    const float sc = 1.f / (steer_scale(J.p) * kLift * ctl->sB);
+    const int ld = B.ld_adj;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < J.Q; i += gridDim.x * blockDim.x) {
+        float y = 0.f;
+        for (int u = 0; u < g.nu; ++u) y += B.padj[(size_t)i * ld + u];
+        out[i] = (double)(y * sc);
     }
 }
 
@@ -1396,6 +1412,26 @@ cudaError_t ws_bounds(WsHost *w, const JobDev &hj, cudaStream_t st) {
         }
         k_ws_bnd_out<<<gq, kWsThreads, 0, st>>>(dj, B, k == 0 ? hj.dirty : hj.h);
     }
+    k_ws_bnd_reset<<<1, 32, 0, st>>>(B);
+    return cudaGetLastError();
+}
+
+cudaError_t ws_psi_adj(WsHost *w, const JobDev &hj, const float2 *U, double *out, cudaStream_t st) {
+    const WsBufs &B = w->B;
+    const JobDev *dj = w->dj;
+    const int sms = w->sms;
+    const size_t asm_ = items_smem_bytes();
+    const int gq = std::min((hj.Q + kWsThreads - 1) / kWsThreads, 4 * sms);
+    k_ws_bnd_reset<<<1, 32, 0, st>>>(B);
+    k_ws_bnd_max<<<sms, kWsThreads, 0, st>>>(dj, B, U, 2);
+    if (w->bf16) {
+        k_ws_emb<true><<<sms, kWsThreads, 0, st>>>(dj, B, 0, U);
+        k_ws_adj<true, false><<<sms, kWideThreads, asm_, st>>>(dj, B);
+    } else {
+        k_ws_emb<false><<<sms, kWsThreads, 0, st>>>(dj, B, 0, U);
+        k_ws_adj<false, false><<<sms, kWideThreads, asm_, st>>>(dj, B);
+    }
+    k_ws_adj_out<<<gq, kWsThreads, 0, st>>>(dj, B, out);
     k_ws_bnd_reset<<<1, 32, 0, st>>>(B);
     return cudaGetLastError();
 }

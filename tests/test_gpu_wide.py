@@ -1,6 +1,7 @@
-"""Wide arrays (64 < p <= 256): the streamed tensor-core adjoint (operand B
+"""Wide arrays (64 < p <= 384): the streamed tensor-core adjoint (operand B
 chunked in global memory, bulk-copied into shared memory per 64-column K
-chunk) against the definitions, evaluated directly in FP64.
+chunk; up to p = 256) and the (tile, unit) work-item adjoint (256 < p <=
+384) against the definitions, evaluated directly in FP64.
 
 * dirty image d_i = a_i^H R a_i and MVDR bound C / (a_i^H R^-1 a_i)
   (Sec. IV-A, Eq. 24), every pixel, ragged tiles and p not a multiple of 8;
@@ -44,7 +45,7 @@ def _direct_bounds(job, bias_c):
 
 @pytest.mark.parametrize("prec", [1, 2])
 @pytest.mark.parametrize("shape", [(65, 21, 13), (96, 24, 20), (128, 16, 16), (130, 9, 31),
-                                   (200, 17, 11), (256, 20, 12)])
+                                   (200, 17, 11), (256, 20, 12), (300, 13, 11), (384, 9, 10)])
 def test_wide_dirty_and_mvdr(G, shape, prec):
     p, nl, nm = shape
     job = synth.custom(700 + p, p, nl, nm, 4, 4 * p + 100, radius=8.0, snr_db=0.0)
@@ -62,7 +63,7 @@ def test_wide_dirty_and_mvdr(G, shape, prec):
 
 
 @pytest.mark.parametrize("prec", [1, 2])
-@pytest.mark.parametrize("p", [72, 160, 256])
+@pytest.mark.parametrize("p", [72, 160, 256, 288, 330])
 def test_wide_psi_adjoint(G, p, prec):
     job = synth.custom(9, p, 19, 14, 2, 4 * p + 100, radius=6.0)
     A = O.steering_matrix(job.ant_xyz, job.l, job.m, job.lam)
@@ -71,7 +72,8 @@ def test_wide_psi_adjoint(G, p, prec):
     U = X + X.conj().T
     im = G.Imager.from_job(job, precision=prec)
     y = im.psi_adj(U)
-    # adjoint identity against the forward operator (CUDA cores above p = 64)
+    # adjoint identity against the forward operator (tensor-core Gram blocks
+    # up to p = 256, CUDA cores above)
     x = rng.random(job.Q)
     K = im.psi(x)
     im.close()
