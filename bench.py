@@ -116,12 +116,14 @@ def make_jobs(seeds, workload: str = "large"):
 
 def default_batch(workload: str, steps: int, sms: int) -> int:
     """Images per step.  mid: two per SM (one CTA each).  large: each image
-    is a graph of kernels spread over the GPU; several solves in flight
-    overlap (8 saturate the GPU to within about 10 %); the batch shrinks to 4
-    when many steps are asked for, to keep the timed region short."""
+    is a graph of kernels spread over the GPU, and the solves in flight
+    overlap: 8 give 0.42 images/s, 16 give 0.54, 24 give 0.55 and 32 fall
+    back to 0.49 (their working sets no longer share L2); the batch shrinks
+    (to 4 at least) when many steps are asked for, to keep the timed region
+    near a minute."""
     if workload == "mid":
         return 2 * sms
-    return max(4, min(8, 96 // max(steps, 1)))
+    return max(4, min(16, 48 // max(steps, 1)))
 
 
 def reduce_max(value: float, device=None) -> float:
@@ -740,7 +742,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=0, help="images per step (0: two per SM)")
     ap.add_argument("--precision", default="f16x3", choices=sorted(PRECISIONS))

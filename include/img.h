@@ -184,7 +184,10 @@ img_status img_dirty(img_ctx *ctx, double *out, int on_device);
 
 /* MVDR upper bound C / (a_i^H R_hat^-1 a_i) (eq. wmvdr with K = 1 and the
  * unbiased form with C, Sec. III-D), inflated as configured, into
- * out[0..Q).  It is the solver's gamma when bound = IMG_BOUND_MVDR. */
+ * out[0..Q).  It is the solver's gamma when bound = IMG_BOUND_MVDR.  The
+ * denominator is evaluated in whitened form, ||L^-1 a_i||^2 with R_hat =
+ * L L^H, in every arithmetic: a sum of squares keeps its rounding error
+ * relative to itself at a bright source, where the quadratic form does not. */
 img_status img_mvdr_bound(img_ctx *ctx, double *out, int on_device);
 
 /* Bounded least-squares image (Table I with LSQR subproblems) into

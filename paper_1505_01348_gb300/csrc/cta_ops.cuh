@@ -96,6 +96,9 @@ __device__ int block_compact(int n, Pred pred, int *out, int *sbuf) {
 // Computes part_j = sum_k Re(conj(A[k][j]) (U A)[k][j]) and leaves the
 // per-pixel sums in red[0..kTile) (valid after the call, before the next
 // __syncthreads of the caller).  U is p x p column-major in global memory.
+// SQ: part_j = ||(U A)[:][j]||^2 instead (with U = L^-1: the whitened MVDR
+// denominator ||L^-1 a_j||^2, whose rounding error is relative to itself).
+template <bool SQ = false>
 __device__ __forceinline__ void adj_chunk(const float2 *U, int p,
                                           const float2 *A, float *red) {
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -128,8 +131,12 @@ __device__ __forceinline__ void adj_chunk(const float2 *U, int p,
                 if (r < nr) {
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
-                        const float2 a = A[(r0 + r) * kTile + tx * 4 + c];
-                        part[c] = fmaf(a.x, y[r][c].x, fmaf(a.y, y[r][c].y, part[c]));
+                        if (SQ) {
+                            part[c] = fmaf(y[r][c].x, y[r][c].x, fmaf(y[r][c].y, y[r][c].y, part[c]));
+                        } else {
+                            const float2 a = A[(r0 + r) * kTile + tx * 4 + c];
+                            part[c] = fmaf(a.x, y[r][c].x, fmaf(a.y, y[r][c].y, part[c]));
+                        }
                     }
                 }
             }

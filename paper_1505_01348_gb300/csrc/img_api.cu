@@ -105,6 +105,7 @@ size_t carve(img_ctx *c, char *base) {
     J.R32 = cv.take<float2>(pp);
     J.Ri32 = cv.take<float2>(pp);
     J.Li32 = cv.take<float2>(pp);
+    J.LiH32 = cv.take<float2>(pp);
     J.El = cv.take<float2>((size_t)nl * p);
     J.Em = cv.take<float2>((size_t)nm * p);
     J.dirty = cv.take<float>(Q);

@@ -50,6 +50,7 @@ struct JobDev {
     float2 *R32;           // R_hat
     float2 *Ri32;          // R_hat^-1
     float2 *Li32;          // L^-1
+    float2 *LiH32;         // L^-H (column n holds the conjugate of row n of L^-1)
     // separable steering tables, pixel-major: El[il*p + k], Em[im*p + k]
     float2 *El;
     float2 *Em;

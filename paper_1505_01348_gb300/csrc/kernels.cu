@@ -124,6 +124,8 @@ __device__ void factor_job(const JobDev &J) {
         }
         J.Ri32[e] = make_float2((float)s.x, (float)s.y);
         J.Li32[e] = make_float2((float)X[e].x, (float)X[e].y);
+        const double2 xt = X[(size_t)a * p + b];               // L^-1(b, a)
+        J.LiH32[e] = make_float2((float)xt.x, (float)-xt.y);
         J.R32[e] = make_float2((float)J.R64[e].x, (float)J.R64[e].y);
     }
     if (threadIdx.x == 0) J.flags[0] = 0;
@@ -132,8 +134,11 @@ __device__ void factor_job(const JobDev &J) {
 __global__ void k_factor(JobDev *const *jobs) { factor_job(*jobs[blockIdx.x]); }
 
 // ---------------------------------------------------------------- bounds
-// dirty_i = Re(a_i^H R a_i) and h_i = Re(a_i^H R^-1 a_i) for all pixels
-// (eq. mfdimg and the MVDR denominator), blockIdx.y = job.
+// dirty_i = Re(a_i^H R a_i) and h_i = a_i^H R^-1 a_i = ||L^-1 a_i||^2 for
+// all pixels (eq. mfdimg and the MVDR denominator, the latter in whitened
+// form: a sum of squares keeps its rounding error relative to h_i, where the
+// quadratic form's error is relative to |a|^T |R^-1| |a|, far larger than h_i
+// at a bright source), blockIdx.y = job.
 __global__ void k_bounds(JobDev *const *jobs) {
     const JobDev &J = *jobs[blockIdx.y];
     if (J.flags[0] != 0) return;
@@ -149,14 +154,15 @@ __global__ void k_bounds(JobDev *const *jobs) {
         adj_chunk(J.R32, J.p, A, red);
         if (threadIdx.x < np) J.dirty[pix0 + threadIdx.x] = red[threadIdx.x];
         __syncthreads();
-        adj_chunk(J.Ri32, J.p, A, red);
+        adj_chunk<true>(J.Li32, J.p, A, red);
         if (threadIdx.x < np) J.h[pix0 + threadIdx.x] = red[threadIdx.x];
         __syncthreads();
     }
 }
 
 // Tensor-core form of k_bounds: pass 1 with B = R_hat (dirty image), pass 2
-// with B = R_hat^-1 (MVDR denominators), over 128-pixel tiles.
+// with B from V = L^-1 and the sum-of-squares epilogue (MVDR denominators
+// ||L^-1 a_i||^2), over 128-pixel tiles.
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1) k_bounds_tc(JobDev *const *jobs) {
     const JobDev &J = *jobs[blockIdx.y];
@@ -177,14 +183,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_bounds_tc(JobDev *const *jobs) 
     const int ntiles = tc_num_tiles(J.n_l, J.n_m);
     const int mine = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     for (int pass = 0; pass < 2; ++pass) {
-        const float sB = tc_build_B<BF>(pass == 0 ? J.R32 : J.Ri32, J.p, T, dbuf);
-        const float inv = 1.f / (sX * sX * sB);
+        const float sB = tc_build_B<BF>(pass == 0 ? J.R32 : J.LiH32, J.p, T, dbuf);
+        const float inv = pass == 0 ? 1.f / (sX * sX * sB) : 1.f / ((sX * sB) * (sX * sB));
         float *dst = pass == 0 ? J.dirty : J.h;
         tc_run_tiles(
             T, mine, idesc,
             [&](int t, int b) { tc_gen_X_steer<BF>(J, T, b, blockIdx.x + t * gridDim.x, sX); },
             [&](int t, int b) {
-                tc_epilogue<BF>(T, b, red);
+                if (pass == 0) tc_epilogue<BF>(T, b, red);
+                else tc_epilogue<BF, true>(T, b, red);
                 if (threadIdx.x < kTcM) {
                     const int i = tc_tile_pixel(blockIdx.x + t * gridDim.x, threadIdx.x, J.n_l, J.n_m);
                     if (i >= 0) dst[i] = red[threadIdx.x] * inv;
@@ -232,16 +239,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_psi_adj_tc(const JobDev *Jp, co
     tc_teardown(T, J.p);
 }
 
-// max |entry| of R_hat (blockIdx.y = 0) and R_hat^-1 (1) per job, 8 blocks
+// max |entry| of R_hat (blockIdx.y = 0) and L^-H (1) per job, 8 blocks
 // each (J.Bmax was zeroed by the factor kernel).
 __global__ void k_emb_max_bounds(JobDev *const *jobs) {
     const JobDev &J = *jobs[blockIdx.x];
     if (J.flags[0] != 0) return;
     const int w = blockIdx.y;
-    emb_absmax(w ? J.Ri32 : J.R32, J.p, blockIdx.z, gridDim.z, J.Bmax + w);
+    emb_absmax(w ? J.LiH32 : J.R32, J.p, blockIdx.z, gridDim.z, J.Bmax + w);
 }
 
-// Chunked B images of R_hat (blockIdx.y = 0) and R_hat^-1 (1) per job; one
+// Chunked B images of R_hat (blockIdx.y = 0) and L^-H (1) per job; one
 // CTA per (64-column chunk, block of kEmbRows rows): blockIdx.z = chunk *
 // (512 / kEmbRows) + row block.
 template <int MODE>
@@ -251,12 +258,13 @@ __global__ void k_emb_bounds(JobDev *const *jobs) {
     const int kc = blockIdx.z / kRB, rb = blockIdx.z - kc * kRB;
     if (J.flags[0] != 0 || kc >= wide_nk(J.p) || rb * kEmbRows >= 2 * wide_kp(J.p)) return;
     const int w = blockIdx.y;
-    emb_B_chunk<MODE == 2>(w ? J.Ri32 : J.R32, J.p, J.Bimg + (size_t)w * wide_B_bytes(J.p), J.Bmax[w],
+    emb_B_chunk<MODE == 2>(w ? J.LiH32 : J.R32, J.p, J.Bimg + (size_t)w * wide_B_bytes(J.p), J.Bmax[w],
                            J.Bscale + w, kc, rb);
 }
 
 // Wide tensor-core bounds for 64 < p <= 256: dirty image (B = R_hat) and
-// a^H R^-1 a (B = R_hat^-1) in one warp-specialised pass over the tiles.
+// a^H R^-1 a = ||L^-1 a||^2 (B from V = L^-1, sum of squares) in one
+// warp-specialised pass over the tiles.
 template <int MODE>
 __global__ void __launch_bounds__(kWideThreads, 1) k_bounds_wide(JobDev *const *jobs) {
     const JobDev &J = *jobs[blockIdx.y];
@@ -270,7 +278,7 @@ __global__ void __launch_bounds__(kWideThreads, 1) k_bounds_wide(JobDev *const *
     const int mine = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     float *dirty = J.dirty, *h = J.h;
     const int to = wide_adjoint<MODE == 2>(J, dyn, bars, &slot, J.Bimg, J.Bimg + wide_B_bytes(J.p), J.Bscale, 2,
-                                           blockIdx.x, gridDim.x, mine,
+                                           blockIdx.x, gridDim.x, mine, 2,
                                            [&](int s, int i, float v) { (s == 0 ? dirty : h)[i] = v; });
     if (to && threadIdx.x == 0) J.flags[2] = IMG_ETIMEOUT;
 }
@@ -297,7 +305,7 @@ __global__ void __launch_bounds__(kWideThreads, 1) k_psi_adj_wide(const JobDev *
     __shared__ uint32_t slot;
     const int ntiles = tc_num_tiles(J.n_l, J.n_m);
     const int mine = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    wide_adjoint<MODE == 2>(J, dyn, bars, &slot, J.Bimg, J.Bimg, J.Bscale, 1, blockIdx.x, gridDim.x, mine,
+    wide_adjoint<MODE == 2>(J, dyn, bars, &slot, J.Bimg, J.Bimg, J.Bscale, 1, blockIdx.x, gridDim.x, mine, 0,
                             [&](int, int i, float v) { out[i] = v; });
 }
 
@@ -723,8 +731,11 @@ __device__ void adjoint_list(const JobDev &J, const float2 *U, const int *pos, i
 }
 
 // Full-image adjoint with generated steering vectors: epi(i, Re(a_i^H U a_i))
-// for every pixel, on one thread per pixel.
-template <int MODE, class Epi, class Pre>
+// for every pixel, on one thread per pixel.  SQ: epi(i, ||V a_i||^2) with V
+// = U on CUDA cores (U column-major) and V = U^H on tensor cores (the B
+// operand's convention), i.e. U = L^-1 resp. L^-H for the whitened MVDR
+// denominator.
+template <int MODE, bool SQ = false, class Epi, class Pre>
 __device__ void adjoint_full(const JobDev &J, const float2 *U, float2 *A, TcWork &T, float *red,
                              double *dbuf, Epi epi, Pre pre) {
     const int Q = J.Q;
@@ -735,7 +746,7 @@ __device__ void adjoint_full(const JobDev &J, const float2 *U, float2 *A, TcWork
             const int np = min(kTile, Q - pix0);
             fill_steer_adj(J, pix0, np, A);
             __syncthreads();
-            adj_chunk(U, J.p, A, red);
+            adj_chunk<SQ>(U, J.p, A, red);
             if (threadIdx.x < np) {
                 pre(pix0 + threadIdx.x);
                 epi(pix0 + threadIdx.x, red[threadIdx.x]);
@@ -746,13 +757,13 @@ __device__ void adjoint_full(const JobDev &J, const float2 *U, float2 *A, TcWork
         constexpr bool BF = MODE == 2;
         const float sB = tc_build_B<BF>(U, J.p, T, dbuf);
         const float sX = steer_scale(J.p);
-        const float inv = 1.f / (sX * sX * sB);
+        const float inv = SQ ? 1.f / ((sX * sB) * (sX * sB)) : 1.f / (sX * sX * sB);
         const uint32_t idesc = idesc_f16(2 * T.Kp, BF ? 1 : 0);
         tc_run_tiles(
             T, tc_num_tiles(J.n_l, J.n_m), idesc,
             [&](int t, int b) { tc_gen_X_steer<BF>(J, T, b, t, sX); },
             [&](int t, int b) {
-                tc_epilogue<BF>(T, b, red);
+                tc_epilogue<BF, SQ>(T, b, red);
                 if (threadIdx.x < kTcM) {
                     const int i = tc_tile_pixel(t, threadIdx.x, J.n_l, J.n_m);
                     if (i >= 0) epi(i, red[threadIdx.x] * inv);
@@ -768,10 +779,10 @@ __device__ void adjoint_full(const JobDev &J, const float2 *U, float2 *A, TcWork
     }
 }
 
-template <int MODE, class Epi>
+template <int MODE, bool SQ = false, class Epi>
 __device__ void adjoint_full(const JobDev &J, const float2 *U, float2 *A, TcWork &T, float *red,
                              double *dbuf, Epi epi) {
-    adjoint_full<MODE>(J, U, A, T, red, dbuf, epi, [](int) {});
+    adjoint_full<MODE, SQ>(J, U, A, T, red, dbuf, epi, [](int) {});
 }
 
 // LSQR (Paige-Saunders) on the free set: min || b - M_F x ||, with
@@ -994,7 +1005,8 @@ k_solve(JobDev *const *jobs, DevInfo *batch_info, double *const *sigma_out) {
         __syncthreads();
         if (J.flags[0] == 0) {
             adjoint_full<MODE>(J, J.R32, A, T, S.red, S.dbuf, [&](int i, float v) { J.dirty[i] = v; });
-            adjoint_full<MODE>(J, J.Ri32, A, T, S.red, S.dbuf, [&](int i, float v) { J.h[i] = v; });
+            adjoint_full<MODE, true>(J, MODE == 0 ? J.Li32 : J.LiH32, A, T, S.red, S.dbuf,
+                                     [&](int i, float v) { J.h[i] = v; });
             finalize_job(J);
         }
         __syncthreads();

@@ -158,10 +158,13 @@ __host__ __device__ inline size_t items_smem_bytes() { return 2 * kWideXStage + 
 // scales; a steering tile's scale is steer_scale(p) kLift).  Needs kWideThreads
 // threads, kWideBars mbarriers and the 1024-aligned dynamic shared memory of
 // items_smem_bytes() - 1024 bytes.  Returns the number of waits that timed out.
+// sq (nkg = 1 only): the partial is the unit's sum of squares ||D[r]||^2
+// instead of the dot (B from V = L^-1: the whitened MVDR denominator
+// ||L^-1 a_i||^2 as the sum of the units' partials, scaled twice).
 template <bool BF16, bool LIST, class Epi>
 __device__ int items_adjoint(const JobDev &J, const UnitGeom &g, unsigned char *dyn, uint64_t *bars, uint32_t *slot,
                              const unsigned char *Bimg, const unsigned char *Ximg, const float2 *vec, const int *pos,
-                             int nrows, int ntiles, int nkg, int first, int stride, Epi epi) {
+                             int nrows, int ntiles, int nkg, int first, int stride, bool sq, Epi epi) {
     const int p = J.p, Kp = g.Kp, nk = g.nk, ku = g.ku, rows_u = unit_rows(g);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *Xs = dyn, *Bs = dyn + 2 * kWideXStage;
@@ -385,7 +388,7 @@ __device__ int items_adjoint(const JobDev &J, const UnitGeom &g, unsigned char *
 #pragma unroll
                 for (int q = 0; q < 16; q += 2) {
                     float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
-                    if (ra && k0 + q < p) {
+                    if (ra && !sq && k0 + q < p) {
                         if (vec2) {
                             const float4 x = __ldg(reinterpret_cast<const float4 *>(ra + k0 + q));
                             a0 = make_float2(x.x, x.y);
@@ -411,8 +414,13 @@ __device__ int items_adjoint(const JobDev &J, const UnitGeom &g, unsigned char *
                 }
                 float dr[16], di[16];
                 tmem_ld16x2(base + kk, base + ku + kk, dr, di);
+                if (sq) {
 #pragma unroll
-                for (int q = 0; q < 16; ++q) acc = fmaf(ar[q], dr[q], fmaf(ai[q], di[q], acc));
+                    for (int q = 0; q < 16; ++q) acc = fmaf(dr[q], dr[q], fmaf(di[q], di[q], acc));
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) acc = fmaf(ar[q], dr[q], fmaf(ai[q], di[q], acc));
+                }
             }
             tc_fence_before();
             __syncwarp();

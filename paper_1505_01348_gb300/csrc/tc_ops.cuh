@@ -547,8 +547,10 @@ __device__ inline void tc_gen_X_cache(const JobDev &J, TcWork &T, int b, const i
 // columns) forms sum_k xs_k D[r][h Kp + k], with xs = hi + lo rebuilt from the
 // operand tile in shared memory (the scaled x the MMA consumed; conflict-free
 // 16-byte reads).  red[r] (r < 128) holds the tile's sums after the call; the
-// caller multiplies by 1/(sX^2 sB).
-template <bool BF16>
+// caller multiplies by 1/(sX^2 sB).  SQ: the sum of squares of the row's
+// accumulator, ||D[r]||^2 (B built from V = L^-1: the whitened MVDR
+// denominator); the caller multiplies by 1/(sX sB)^2.
+template <bool BF16, bool SQ = false>
 __device__ inline void tc_epilogue(const TcWork &T, int b, float *red) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int half = warp >> 2, r = 32 * (warp & 3) + lane;
@@ -559,34 +561,41 @@ __device__ inline void tc_epilogue(const TcWork &T, int b, float *red) {
         float dd[2][16];
         const uint32_t ta = T.tmem + lane_base + (uint32_t)(b * 2 * T.Kp + half * T.Kp + c00);
         tmem_ld16x2(ta, ta + 16, dd[0], dd[1]);
+        if (SQ) {
 #pragma unroll
-        for (int g = 0; g < 2; ++g) {
-        const int c0 = c00 + 16 * g;
-        const float *d = dd[g];
+            for (int g = 0; g < 2; ++g)
 #pragma unroll
-        for (int s8 = 0; s8 < 2; ++s8) {
-            const uint32_t off = sw128_off(r, half * nc8 + c0 / 8 + s8, kTcM);
-            const uint4 h4 = *reinterpret_cast<const uint4 *>(T.Xhi[b] + off);
-            const uint4 l4 = *reinterpret_cast<const uint4 *>(T.Xlo[b] + off);
-            const uint32_t hw[4] = {h4.x, h4.y, h4.z, h4.w}, lw[4] = {l4.x, l4.y, l4.z, l4.w};
+                for (int q = 0; q < 16; ++q) acc = fmaf(dd[g][q], dd[g][q], acc);
+        } else {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                float h0, h1, l0, l1;
-                if (BF16) {
-                    h0 = __uint_as_float(hw[q] << 16);
-                    h1 = __uint_as_float(hw[q] & 0xffff0000u);
-                    l0 = __uint_as_float(lw[q] << 16);
-                    l1 = __uint_as_float(lw[q] & 0xffff0000u);
-                } else {
-                    h0 = __half2float(__ushort_as_half((unsigned short)(hw[q] & 0xffffu)));
-                    h1 = __half2float(__ushort_as_half((unsigned short)(hw[q] >> 16)));
-                    l0 = __half2float(__ushort_as_half((unsigned short)(lw[q] & 0xffffu)));
-                    l1 = __half2float(__ushort_as_half((unsigned short)(lw[q] >> 16)));
+            for (int g = 0; g < 2; ++g) {
+            const int c0 = c00 + 16 * g;
+            const float *d = dd[g];
+#pragma unroll
+            for (int s8 = 0; s8 < 2; ++s8) {
+                const uint32_t off = sw128_off(r, half * nc8 + c0 / 8 + s8, kTcM);
+                const uint4 h4 = *reinterpret_cast<const uint4 *>(T.Xhi[b] + off);
+                const uint4 l4 = *reinterpret_cast<const uint4 *>(T.Xlo[b] + off);
+                const uint32_t hw[4] = {h4.x, h4.y, h4.z, h4.w}, lw[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float h0, h1, l0, l1;
+                    if (BF16) {
+                        h0 = __uint_as_float(hw[q] << 16);
+                        h1 = __uint_as_float(hw[q] & 0xffff0000u);
+                        l0 = __uint_as_float(lw[q] << 16);
+                        l1 = __uint_as_float(lw[q] & 0xffff0000u);
+                    } else {
+                        h0 = __half2float(__ushort_as_half((unsigned short)(hw[q] & 0xffffu)));
+                        h1 = __half2float(__ushort_as_half((unsigned short)(hw[q] >> 16)));
+                        l0 = __half2float(__ushort_as_half((unsigned short)(lw[q] & 0xffffu)));
+                        l1 = __half2float(__ushort_as_half((unsigned short)(lw[q] >> 16)));
+                    }
+                    acc = fmaf(h0 + l0, d[s8 * 8 + 2 * q], acc);
+                    acc = fmaf(h1 + l1, d[s8 * 8 + 2 * q + 1], acc);
                 }
-                acc = fmaf(h0 + l0, d[s8 * 8 + 2 * q], acc);
-                acc = fmaf(h1 + l1, d[s8 * 8 + 2 * q + 1], acc);
             }
-        }
+            }
         }
     }
     red[half * kTcM + r] = acc;

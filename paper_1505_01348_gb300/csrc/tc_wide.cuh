@@ -197,13 +197,15 @@ __device__ __forceinline__ void wide_wait(uint64_t *bars, int slot, uint32_t &ph
 
 // out = Re(a_i^H U_s a_i) for npass <= 2 operators s (B images B0, B1,
 // scales sB[s]) over the 2-D tiles t0, t0 + dt, ... (ntiles of them);
-// epi(s, i, v) receives each pixel's value.  Needs kWideThreads threads,
+// epi(s, i, v) receives each pixel's value.  Bit s of sq_mask makes pass s
+// a sum of squares instead, out = ||V_s a_i||^2 with V_s = U_s^H (the B
+// image of U_s = L^-H gives the whitened MVDR denominator ||L^-1 a_i||^2).  Needs kWideThreads threads,
 // 1024-aligned dynamic shared memory `dyn` of wide_smem_bytes(p) - 1024
 // bytes and kWideBars mbarriers.  Returns the number of waits that timed out.
 template <bool BF16, class Epi>
 __device__ int wide_adjoint(const JobDev &J, unsigned char *dyn, uint64_t *bars, uint32_t *slot,
                             const unsigned char *B0, const unsigned char *B1, const float *sB, int npass,
-                            int t0, int dt, int ntiles, Epi epi) {
+                            int t0, int dt, int ntiles, int sq_mask, Epi epi) {
     const int p = J.p, Kp = wide_kp(p), nk = wide_nk(p), nu = wide_units(p), rows_u = wide_unit_rows(p);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *Xs = dyn, *Bs = dyn + 2 * kWideXStage;
@@ -421,6 +423,7 @@ __device__ int wide_adjoint(const JobDev &J, unsigned char *dyn, uint64_t *bars,
             issue(0);
             issue(1);
             const int i = tc_tile_pixel(t, r, nl, nm);
+            const bool sq = (sq_mask >> pass) & 1;
             float acc = 0.f;
             int grp = 0;
             for (int pp = 0; pp < nu; ++pp) {
@@ -448,15 +451,25 @@ __device__ int wide_adjoint(const JobDev &J, unsigned char *dyn, uint64_t *bars,
                     }
                     float dr[16], di[16];
                     tmem_ld16x2(base + kk, base + wcols + kk, dr, di);
+                    if (sq) {
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) acc = fmaf(ar[q], dr[q], fmaf(ai[q], di[q], acc));
+                        for (int q = 0; q < 16; ++q) acc = fmaf(dr[q], dr[q], fmaf(di[q], di[q], acc));
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) acc = fmaf(ar[q], dr[q], fmaf(ai[q], di[q], acc));
+                    }
                     __syncwarp();
                 }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&bars[kAEmpty + g]);
             }
-            if (i >= 0) epi(pass, i, acc / (sX * sB[pass]));
+            if (i >= 0) {
+                // the steering side entered the MMA scaled by sX, the dot above
+                // unscaled; a sum of squares carries both scales twice
+                const float sc = sq ? (sX * sB[pass]) * (sX * sB[pass]) : sX * sB[pass];
+                epi(pass, i, acc / sc);
+            }
         }
     }
     if (timeouts) atomicAdd(&s_timeouts, timeouts);

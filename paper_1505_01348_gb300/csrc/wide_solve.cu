@@ -31,8 +31,10 @@ namespace img {
 constexpr int kWsThreads = 256;
 // Grid of the list kernels (forward, free-list adjoint): a share of the SMs,
 // so that the kernels of several solves in flight pack next to each other;
-// the full-image adjoint of the gradient takes every SM.
-constexpr int kListGrid = 64;
+// the full-image adjoint of the gradient takes every SM.  32 measured best
+// for 16 solves of 256x256, p = 288 in flight (0.54 images/s; 64 CTAs:
+// 0.48, 48: 0.51, 16: 0.53); fewer CTAs also mean fewer forward splits.
+constexpr int kListGrid = 32;
 constexpr int kWsSums = 2048;           // per-CTA partial sums of the reductions
 
 // Device control block of one wide solve.
@@ -57,6 +59,7 @@ struct WsCtl {
     unsigned cond[4];           // last value of each loop / branch condition (host-driven mode)
     int cache_slot, cache_pixel; // support slot whose vectors k_ws_cache computes (-1: none)
     int nsums;                  // CTA shares of ||t||^2 left in sums by k_ws_fred
+    int adj_sq;                 // full-image adjoint as sums of squares (MVDR denominators)
     unsigned long long launches;  // kernels executed in this solve
     double sums[kWsSums];
 };
@@ -674,8 +677,9 @@ __global__ void __launch_bounds__(kWideThreads, 1) k_ws_adj(const JobDev *Jp, Ws
     __shared__ uint32_t tslot;
     float *out = B.padj;
     const int ld = B.ld_adj;
+    const bool sq = !LIST && ctl->adj_sq;
     const int to = items_adjoint<BF16, LIST>(
-        J, g, dyn, bars, &tslot, B.bimg, B.ximgF, J.cvec, J.fpos, n, ntiles, nkg, blockIdx.x, gridDim.x,
+        J, g, dyn, bars, &tslot, B.bimg, B.ximgF, J.cvec, J.fpos, n, ntiles, nkg, blockIdx.x, gridDim.x, sq,
         [&](int u, int t, int r, float v) {
             if (LIST) {
                 const int j = t * kTcM + r;
@@ -735,20 +739,37 @@ __global__ void __launch_bounds__(kVxThreads) k_ws_vx(const JobDev *Jp, WsBufs B
     const float sc = 1.f / (ctl->sXF * ctl->sB);
     const float fus = (float)us, fb = (float)beta;
     float ss = 0.f;
-    for (int j = threadIdx.x; j < f; j += blockDim.x) {
-        float y = 0.f;
-        const float4 *pr = reinterpret_cast<const float4 *>(B.padj + (size_t)j * ld);
-        const int r4 = rows >> 2;
-        float4 s4[9];                                   // rows <= nu nk <= 36
+    const int r4 = rows >> 2;
+    float *__restrict__ vv = J.v;
+    const float *__restrict__ sF = J.sF;
+    // two rows per thread per step: every load of both rows is in flight
+    // before the sums (rows <= nu nk <= 36 partial dots, 9 float4)
+    for (int j0 = threadIdx.x; j0 < f; j0 += 2 * blockDim.x) {
+        float4 s4[2][9];
+        float vo[2], sf[2];
 #pragma unroll
-        for (int q = 0; q < 9; ++q) s4[q] = q < r4 ? pr[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int h = 0; h < 2; ++h) {
+            const int j = j0 + h * blockDim.x;
+            const bool ok = j < f;
+            const float4 *pr = reinterpret_cast<const float4 *>(B.padj + (size_t)(ok ? j : 0) * ld);
 #pragma unroll
-        for (int q = 0; q < 9; ++q) y += (s4[q].x + s4[q].y) + (s4[q].z + s4[q].w);
-        for (int u = 4 * r4; u < rows; ++u) y += B.padj[(size_t)j * ld + u];
-        y *= sc;
-        const float vn = init ? J.sF[j] * (y * fus) : J.sF[j] * (y * fus) - fb * J.v[j];
-        J.v[j] = vn;
-        ss = fmaf(vn, vn, ss);
+            for (int q = 0; q < 9; ++q) s4[h][q] = (ok && q < r4) ? pr[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+            sf[h] = ok ? sF[j] : 0.f;
+            vo[h] = (ok && !init) ? vv[j] : 0.f;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int j = j0 + h * blockDim.x;
+            if (j >= f) continue;
+            float y = 0.f;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) y += (s4[h][q].x + s4[h][q].y) + (s4[h][q].z + s4[h][q].w);
+            for (int u = 4 * r4; u < rows; ++u) y += B.padj[(size_t)j * ld + u];
+            y *= sc;
+            const float vn = init ? sf[h] * (y * fus) : sf[h] * (y * fus) - fb * vo[h];
+            vv[j] = vn;
+            ss = fmaf(vn, vn, ss);
+        }
     }
     const double alpha = sqrt(vx_sum((double)ss, sb));
     double rhobar = ctl->rhobar, phibar = ctl->phibar, anorm2 = ctl->anorm2, t1 = 0.0, t2 = 0.0, absc = 0.0;
@@ -770,6 +791,7 @@ __global__ void __launch_bounds__(kVxThreads) k_ws_vx(const JobDev *Jp, WsBufs B
     }
     const float ia = alpha > 0.0 ? (float)(1.0 / alpha) : 1.f, ft1 = (float)t1, ft2 = (float)t2;
     float xs2 = 0.f, wm = 0.f;
+#pragma unroll 4
     for (int j = threadIdx.x; j < f; j += blockDim.x) {
         const float vj = J.v[j] * ia;
         J.v[j] = vj;
@@ -998,9 +1020,10 @@ __global__ void k_ws_step(const JobDev *Jp, WsBufs B) {
 // pixel, from the unit image of U.  k_ws_bnd_max readies the control block
 // (no solve runs on the context meanwhile) and reduces max |U|;
 // k_ws_bnd_out sums each pixel's unit partial dots.
-__global__ void k_ws_bnd_max(const JobDev *Jp, WsBufs B, const float2 *U, int first) {
+__global__ void k_ws_bnd_max(const JobDev *Jp, WsBufs B, const float2 *U, int first, int sq) {
     const JobDev &J = *Jp;
     WsCtl *ctl = B.ctl;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->adj_sq = sq;
     if (first && blockIdx.x == 0 && threadIdx.x == 0) {
         // bounds (first = 1): a failed factor leaves them alone; the
         // stand-alone adjoint (first = 2) does not depend on the factor
@@ -1021,7 +1044,8 @@ __global__ void k_ws_bnd_out(const JobDev *Jp, WsBufs B, float *out) {
     if (ctl->timeouts && blockIdx.x == 0 && threadIdx.x == 0) J.flags[2] = IMG_ETIMEOUT;
     if (ctl->stop) return;
     const UnitGeom g = unit_geom(J.p);
-    const float sc = 1.f / (steer_scale(J.p) * kLift * ctl->sB);
+    const float s1 = steer_scale(J.p) * kLift * ctl->sB;
+    const float sc = ctl->adj_sq ? 1.f / (s1 * s1) : 1.f / s1;
     const int ld = B.ld_adj;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < J.Q; i += gridDim.x * blockDim.x) {
         float y = 0.f;
@@ -1045,7 +1069,10 @@ __global__ void k_ws_adj_out(const JobDev *Jp, WsBufs B, double *out) {
 }
 
 __global__ void k_ws_bnd_reset(WsBufs B) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) B.ctl->mx_t = 0u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        B.ctl->mx_t = 0u;
+        B.ctl->adj_sq = 0;                    // the solve's adjoints are dots
+    }
 }
 
 // ================================================================ host side
@@ -1400,9 +1427,11 @@ cudaError_t ws_bounds(WsHost *w, const JobDev &hj, cudaStream_t st) {
     const size_t asm_ = items_smem_bytes();
     const int gq = std::min((hj.Q + kWsThreads - 1) / kWsThreads, 4 * sms);
     for (int k = 0; k < 2; ++k) {
-        const float2 *U = k == 0 ? hj.R32 : hj.Ri32;
+        // dirty image from R_hat; MVDR denominators ||L^-1 a||^2 from the B
+        // image of L^-H (V = L^-1) with the sum-of-squares epilogue
+        const float2 *U = k == 0 ? hj.R32 : hj.LiH32;
         k_ws_bnd_reset<<<1, 32, 0, st>>>(B);
-        k_ws_bnd_max<<<sms, kWsThreads, 0, st>>>(dj, B, U, k == 0);
+        k_ws_bnd_max<<<sms, kWsThreads, 0, st>>>(dj, B, U, k == 0, k);
         if (w->bf16) {
             k_ws_emb<true><<<sms, kWsThreads, 0, st>>>(dj, B, 0, U);
             k_ws_adj<true, false><<<sms, kWideThreads, asm_, st>>>(dj, B);
@@ -1423,7 +1452,7 @@ cudaError_t ws_psi_adj(WsHost *w, const JobDev &hj, const float2 *U, double *out
     const size_t asm_ = items_smem_bytes();
     const int gq = std::min((hj.Q + kWsThreads - 1) / kWsThreads, 4 * sms);
     k_ws_bnd_reset<<<1, 32, 0, st>>>(B);
-    k_ws_bnd_max<<<sms, kWsThreads, 0, st>>>(dj, B, U, 2);
+    k_ws_bnd_max<<<sms, kWsThreads, 0, st>>>(dj, B, U, 2, 0);
     if (w->bf16) {
         k_ws_emb<true><<<sms, kWsThreads, 0, st>>>(dj, B, 0, U);
         k_ws_adj<true, false><<<sms, kWideThreads, asm_, st>>>(dj, B);
