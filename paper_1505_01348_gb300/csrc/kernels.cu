@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bounds_tc(JobDev *const *jobs) 
     TcWork T{};
     tc_carve(T, dyn, J.p);
     tc_setup(T, bars, &slot, J.p);
-    const float sX = steer_scale(J.p);
+    const float sX = tc_steer_scale(J.p);
     const uint32_t idesc = idesc_f16(2 * T.Kp, BF ? 1 : 0);
     const int ntiles = tc_num_tiles(J.n_l, J.n_m);
     const int mine = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_psi_adj_tc(const JobDev *Jp, co
     TcWork T{};
     tc_carve(T, dyn, J.p);
     tc_setup(T, bars, &slot, J.p);
-    const float sX = steer_scale(J.p);
+    const float sX = tc_steer_scale(J.p);
     const uint32_t idesc = idesc_f16(2 * T.Kp, BF ? 1 : 0);
     const float sB = tc_build_B<BF>(U, J.p, T, dbuf);
     const float inv = 1.f / (sX * sX * sB);
@@ -660,7 +660,8 @@ __device__ void cache_vector(const JobDev &J, int i, int slot, double *sbuf) {
     __syncthreads();
 }
 
-// Power-of-two scale for the cached vectors of a list (max |entry| <= 1).
+// Power-of-two scale for the cached vectors of a list (max |entry| <= 1),
+// lifted by kLift (the tiles' split parts stay normal FP16 numbers).
 __device__ float list_scale(const JobDev &J, const int *pos, int n, double *sbuf) {
     float mx = 0.f;
     for (int j = threadIdx.x; j < n; j += blockDim.x) mx = fmaxf(mx, J.cmax[pos ? pos[j] : j]);
@@ -670,7 +671,7 @@ __device__ float list_scale(const JobDev &J, const int *pos, int n, double *sbuf
     mx = 0.f;
     for (int w = 0; w < kThreads / 32; ++w) mx = fmaxf(mx, (float)sbuf[w]);
     __syncthreads();
-    return mx > 0.f ? exp2f(-ceilf(log2f(mx))) : 1.f;
+    return (mx > 0.f ? exp2f(-ceilf(log2f(mx))) : 1.f) * kLift;
 }
 
 // K = base + sum_j wt[j] c_j c_j^H over a list of cached vectors, on tensor
@@ -756,7 +757,7 @@ __device__ void adjoint_full(const JobDev &J, const float2 *U, float2 *A, TcWork
     } else {
         constexpr bool BF = MODE == 2;
         const float sB = tc_build_B<BF>(U, J.p, T, dbuf);
-        const float sX = steer_scale(J.p);
+        const float sX = tc_steer_scale(J.p);
         const float inv = SQ ? 1.f / ((sX * sB) * (sX * sB)) : 1.f / (sX * sX * sB);
         const uint32_t idesc = idesc_f16(2 * T.Kp, BF ? 1 : 0);
         tc_run_tiles(
@@ -1316,7 +1317,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_psi_partial_tc(const JobDev *Jp
     tc_setup(T, bars, &slot, J.p);
     const int i0 = blockIdx.x * per;
     const int n = max(0, min(per, J.Q - i0));
-    const float sX = steer_scale(J.p);
+    const float sX = tc_steer_scale(J.p);
     tc_forward<BF>(T, J.p, n, wx + i0, sX,
                    [&](int t, int np) { tc_gen_X_range<BF>(J, T, 0, i0 + t * kTcM, np, sX); },
                    nullptr, false, part + (size_t)blockIdx.x * J.p * J.p, dbuf);

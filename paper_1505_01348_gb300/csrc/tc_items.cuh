@@ -36,15 +36,6 @@ namespace img {
 constexpr int kItemsMaxP = 384;
 constexpr size_t kListBlock = (size_t)2 * kTcM * 128;    // one (tile, chunk) block, hi + lo: 32 KB
 
-// Operand scale lift.  FP16 holds full precision only in its normal range
-// [2^-14, 2^15]; the lo part of a split value is about 2^-11 of the value, so
-// with operands scaled to a maximum near 1 the lo part of every value below
-// 1/8 of the maximum would be subnormal and lose bits.  Operands are scaled
-// to a maximum near 2^13 instead: lo parts stay normal for values down to
-// about 2^-16 of the maximum.  Products stay below 2^28 and accumulated
-// sums far below the FP32 range.  (BF16 parts have the FP32 exponent range;
-// the lift is harmless there.)
-constexpr float kLift = 8192.f;
 
 struct UnitGeom {
     int Kp;     // padded antenna count (multiple of 32)

@@ -258,8 +258,18 @@ __device__ inline void tc_teardown(TcWork &T, int p) {
     if (threadIdx.x < 32) tmem_dealloc(T.tmem, tc_tmem_cols(p));
 }
 
+// Operand scale lift.  FP16 holds full precision only in its normal range
+// [2^-14, 2^15]; the lo part of a split value is about 2^-11 of the value, so
+// with operands scaled to a maximum near 1 the lo part of every value below
+// 1/8 of the maximum would be subnormal and lose bits.  Operands are scaled
+// to a maximum near 2^13 instead: lo parts stay normal for values down to
+// about 2^-16 of the maximum.  Products stay below 2^28 and accumulated
+// sums far below the FP32 range.  (BF16 parts have the FP32 exponent range;
+// the lift is harmless there.)
+constexpr float kLift = 8192.f;
+
 // B = real embedding of U, scaled by a power of two to max |entry| <= 1,
-// split into hi/lo 16-bit tiles.  Row n of B^T (N index) holds, for
+// lifted by kLift and split into hi/lo 16-bit tiles.  Row n of B^T (N index) holds, for
 // n < p: [Re V(n,:), -Im V(n,:)], for Kp <= n < Kp+p: [Im V(n,:), Re V(n,:)]
 // with V = U^H; Re(a^H U a) = Re(a^H U^H a), and row n of V is the conjugate
 // of column n of U, which is contiguous.  One pass: each thread keeps its
@@ -302,7 +312,7 @@ __device__ float tc_build_B(const float2 *U, int p, TcWork &T, double *sbuf) {
     mx = 0.f;
     for (int w = 0; w < kThreads / 32; ++w) mx = fmaxf(mx, (float)sbuf[w]);
     __syncthreads();
-    const float sc = mx > 0.f ? exp2f(-ceilf(log2f(mx))) : 1.f;
+    const float sc = (mx > 0.f ? exp2f(-ceilf(log2f(mx))) : 1.f) * kLift;
 #pragma unroll
     for (int q = 0; q < kMaxItems; ++q) {
         const int it = threadIdx.x + q * kThreads;
@@ -605,7 +615,11 @@ __device__ inline void tc_epilogue(const TcWork &T, int b, float *red) {
     __syncthreads();
 }
 
+
 __device__ __forceinline__ float steer_scale(int p) { return exp2f(floorf(0.5f * log2f((float)p))); }
+// Scale of the steering tiles of the one-CTA tensor-core paths (p <= 64):
+// unit range, lifted as above.
+__device__ __forceinline__ float tc_steer_scale(int p) { return steer_scale(p) * kLift; }
 
 }  // namespace img
 

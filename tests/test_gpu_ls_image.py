@@ -55,6 +55,27 @@ def test_ls_image_matches_oracle(G, shape, cost, prec):
     assert np.linalg.norm(g) <= 10 * tol * np.linalg.norm(g0)
 
 
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("cost", [0, 1])
+@pytest.mark.parametrize("shape", [(72, 14, 12), (130, 12, 11)])
+def test_ls_image_wide_arrays_match_oracle(G, shape, cost, prec):
+    """p > 64: the tensor-core arithmetics run the streamed adjoint and the
+    Gram-block forward (two B units at Kp = 160)."""
+    p, nl, nm = shape
+    job = synth.custom(60 + p, p, nl, nm, 3, 20 * p, radius=8.0, snr_db=5.0)
+    prob, ref = _oracle(job, cost)
+    im = G.Imager.from_job(job, cost=cost, precision=prec, lsqr_atol=1e-7, lsqr_btol=1e-7)
+    sigma, info = im.ls_image(maxit=600)
+    im.close()
+    assert info.converged == 1
+    tol = IMG_TOL if prec != 2 else 1e-3
+    assert _rel(sigma, ref) <= tol
+    x = sigma / prob.to_sigma
+    g = np.real(prob.M.conj().T @ (prob.b - prob.M @ x))
+    g0 = np.real(prob.M.conj().T @ prob.b)
+    assert np.linalg.norm(g) <= 10 * tol * np.linalg.norm(g0)
+
+
 def test_ls_image_errors_and_repeat(G):
     job = synth.custom(7, 12, 8, 8, 2, 500, radius=3.0)
     im = G.Imager(job.ant_xyz, job.l, job.m)
