@@ -36,6 +36,14 @@ constexpr int kWsThreads = 256;
 // 0.48, 48: 0.51, 16: 0.53); fewer CTAs also mean fewer forward splits.
 constexpr int kListGrid = 32;
 constexpr int kWsSums = 2048;           // per-CTA partial sums of the reductions
+// 64-pixel stages per forward task (at least).  Fewer, longer tasks write
+// fewer partial blocks for the reduction to read back (16 solves of 256x256,
+// p = 288 in flight: 4 -> 0.539, 8 -> 0.551, 16 -> 0.561 images/s), but the
+// split also fixes the order of the forward's partial sums, and with 4 the
+// complete 256x256, p = 288 solve takes the FP64 oracle's decisions one for
+// one at the same LSQR tolerance (with 16 a tie at decision 2013 of 2797
+// falls the other way).
+constexpr int kFwdPerTask = 4;
 
 // Device control block of one wide solve.
 struct WsCtl {
@@ -85,6 +93,7 @@ struct WsBufs {
     unsigned char *ximgF, *ximgS, *ximgW, *bimg;   // list images: F, U or support, weighted; B image
     int npairs, pm[kItemsFwdMaxPairs], pnb[kItemsFwdMaxPairs];
     int max_tasks;              // capacity of pfwd in blocks
+    int fwd_per;                // 64-pixel stages per forward task (at least)
     int nrows_adj;              // rows of padj (max(Q, cap))
     int ld_adj;                 // partial dots per row of padj (nu nk)
 };
@@ -314,9 +323,9 @@ __device__ int ws_nkg(int items, int nk, int grid) {
     return best;
 }
 
-__device__ int ws_nsplit(int n, int npairs, int max_tasks) {
+__device__ int ws_nsplit(int n, int npairs, int max_tasks, int per) {
     const int stages = (n + kFwdPix - 1) / kFwdPix;
-    int ns = (stages + 3) / 4;                     // about four stages per task
+    int ns = (stages + per - 1) / per;             // about `per` stages per task
     const int cap = max(1, max_tasks / max(npairs, 1));
     ns = min(ns, cap);
     return max(ns, 1);
@@ -409,7 +418,7 @@ __global__ void k_ws_pass(const JobDev *Jp, WsBufs B, cudaGraphConditionalHandle
         ctl->sXF = pow2_scale(mF) * kLift;
         ctl->sXS = pow2_scale(mU) * kLift;
         ctl->mx_w = __float_as_uint(wm);
-        ctl->nsplit = ws_nsplit(nu, B.npairs, B.max_tasks);
+        ctl->nsplit = ws_nsplit(nu, B.npairs, B.max_tasks, B.fwd_per);
         ctl->maxit = J.lsqr_maxit > 0 ? J.lsqr_maxit : 4 * f + 20;
         ctl->it = 0;
         ctl->op_flops += ws_flops_fwd(J.p, nu);
@@ -839,7 +848,7 @@ __global__ void __launch_bounds__(kVxThreads) k_ws_vx(const JobDev *Jp, WsBufs B
         // the next forward: t <- M v - alpha u with u = t us, so fa = alpha us
         ctl->fa = alpha * us;
         ctl->nlist = f;
-        ctl->nsplit = ws_nsplit(f, B.npairs, B.max_tasks);
+        ctl->nsplit = ws_nsplit(f, B.npairs, B.max_tasks, B.fwd_per);
         ws_cond(ctl, kCondLsqr, h_lsqr, more ? 1u : 0u);
     }
 }
@@ -909,7 +918,7 @@ __global__ void k_ws_accept(const JobDev *Jp, WsBufs B) {
         ctl->mx_w = __float_as_uint(wm);
         ctl->sXS = pow2_scale(mS) * kLift;
         ctl->nlist = ns;
-        ctl->nsplit = ws_nsplit(ns, B.npairs, B.max_tasks);
+        ctl->nsplit = ws_nsplit(ns, B.npairs, B.max_tasks, B.fwd_per);
         ctl->key = ~0ull;
         ctl->op_flops += ws_flops_fwd(J.p, ns) + ws_flops_adj(J.p, J.Q);
     }
@@ -1160,6 +1169,7 @@ size_t ws_bytes(const JobDev &hj, int sms, WsBufs *B, char *base) {
     WsBufs b{};
     b.npairs = items_fwd_pairs(g, b.pm, b.pnb);
     b.max_tasks = std::max(b.npairs, 2 * std::min(sms, kListGrid));
+    b.fwd_per = kFwdPerTask;
     b.nrows_adj = std::max(hj.Q, cap);
     b.ld_adj = (g.nu * g.nk + 3) / 4 * 4;    // a multiple of 4: rows read as float4
     b.ctl = reinterpret_cast<WsCtl *>(take(sizeof(WsCtl)));
