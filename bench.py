@@ -273,9 +273,10 @@ def unit_kp(p: int) -> int:
 def run_operators(args, cases=((64, 256), (128, 256), (256, 256), (256, 512), (288, 256)), reps: int = 20):
     """Operator pair img_psi_adj / img_psi on full n x n grids: p = 64, 128
     and 256 on 256x256 (the serving mix's largest grid), p = 256 on 512x512
-    and p = 288 on 256x256; up to p = 256 both run the streamed,
-    warp-specialised tensor-core kernels; at p = 288 the adjoint runs the
-    solver's (tile, unit) work-item kernel and the forward CUDA cores.
+    and p = 288 on 256x256; up to p = 256 the adjoint runs the streamed,
+    warp-specialised tensor-core kernel and at p = 288 the solver's (tile,
+    unit) work-item kernel; the forward forms tensor-core Gram blocks at
+    every p.
     Adjoint Psi^H (Eq. 16): the streamed tensor-core kernel; each call reduces
     max |U|, writes the chunked operand image from the complex128 U and runs
     the adjoint; calls are queued back to back on one stream and timed with
@@ -338,14 +339,7 @@ def run_operators(args, cases=((64, 256), (128, 256), (256, 256), (256, 512), (2
         torch.cuda.synchronize()
         tf = e0.elapsed_time(e1) / 1e3 / reps
         im2.close()
-        if p > 256:
-            # the forward runs on CUDA cores above p = 256
-            rec.update({"forward_us_per_call": tf * 1e6,
-                        "forward_useful_tflops": 4.0 * p * p * job.Q / tf / 1e12,
-                        "forward_kernel": "CUDA cores (k_psi_partial + k_psi_reduce)"})
-            out_d[f"p{p}_{n}"] = rec
-            continue
-        nf = 2 * kp
+        nf = 2 * ((p + 31) // 32 * 32)
         blocks = [(m, nb) for m in range((nf + 127) // 128) for nb in range((nf + 255) // 256)
                   if 256 * nb + min(256, nf - 256 * nb) - 1 >= 128 * m]
         pix = ((n + 7) // 8) * ((n + 7) // 8) * 64

@@ -73,8 +73,8 @@ enum { IMG_C64 = 0, IMG_C128 = 1 };
  * p = 64 the whole Table I loop of a job runs in one CTA; above that it runs
  * as one CUDA graph per job (its loop and branches in device-side
  * conditional nodes) whose kernels spread each product over the GPU.  The
- * stand-alone operators use them up to p = 256 (img_psi) or p = 384
- * (img_psi_adj and the dirty / MVDR images).  IMG_PREC_FP32 runs
+ * stand-alone operators (img_psi, img_psi_adj, the dirty / MVDR images)
+ * use them up to p = 384 as well.  IMG_PREC_FP32 runs
  * everything on CUDA cores, the solver in one CTA per job. */
 enum { IMG_PREC_FP32 = 0,       /* FP32 on CUDA cores                        */
        IMG_PREC_F16X3 = 1,      /* split FP16, power-of-two scaled: ~FP32    */
@@ -224,7 +224,7 @@ img_status img_psi(img_ctx *ctx, const double *x, double *Kout, int on_device);
  * warp-specialised kernel that streams the operand from global memory, for
  * 256 < p <= 384 on the solver's (tile, unit) work-item kernel (whose
  * buffers the first such call allocates); the forward (img_psi) forms
- * tensor-core Gram blocks up to p = 256 and runs on CUDA cores above.
+ * tensor-core Gram blocks up to p = 384.
  * img_psi and img_psi_adj also take on_device = 2: device pointers, work
  * queued on the context's stream and the call returns without waiting
  * (the caller orders or synchronises with that stream). */

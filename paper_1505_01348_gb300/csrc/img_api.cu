@@ -136,7 +136,7 @@ size_t carve(img_ctx *c, char *base) {
     J.ev_count = cv.take<int>(1);
     J.Bimg = p <= img::kMaxWideP ? cv.take<unsigned char>(2 * img::wide_B_bytes(p)) : nullptr;
     J.Bscale = cv.take<float>(2);
-    J.Bmax = p <= img::kMaxWideP ? cv.take<unsigned>(2) : nullptr;
+    J.Bmax = cv.take<unsigned>(2);           // also the forward's max |w| word at every p
     J.info = cv.take<DevInfo>(1);
     J.flags = cv.take<int>(4);
     c->dj = cv.take<JobDev>(1);
@@ -160,6 +160,12 @@ int mode_of(const img_ctx *c) {
 // img_psi / img_psi_adj use the pipelined streamed kernels at every p.
 int op_mode_of(const img_ctx *c) {
     return (c->prm.precision != IMG_PREC_FP32 && c->prm.p <= img::kMaxWideP) ? c->prm.precision : 0;
+}
+
+// Arithmetic of the stand-alone forward (img_psi): tensor-core Gram blocks up
+// to p = 384, or 0 for CUDA cores.
+int fwd_mode_of(const img_ctx *c) {
+    return (c->prm.precision != IMG_PREC_FP32 && c->prm.p <= img::kMaxWideFwdP) ? c->prm.precision : 0;
 }
 
 // Arithmetic of the graph-driven wide solver (64 < p <= 384, tensor cores),
@@ -546,7 +552,7 @@ img_status img_psi(img_ctx *c, const double *x, double *Kout, int on_device) {
         CK(cudaMemcpyAsync(c->wx, f.data(), Q * sizeof(float), cudaMemcpyHostToDevice, c->stream));
         CK(cudaStreamSynchronize(c->stream));
     }
-    const int om = op_mode_of(c);
+    const int om = fwd_mode_of(c);
     if (om != 0) {
         // tensor-core Gram blocks; their partial sums need a scratch buffer
         if (!c->fwd_part) {

@@ -199,6 +199,7 @@ size_t solve_smem_bytes(int p, int mode);
 constexpr int kMaxTcP = 64;   // tensor-core solver: 2p x 2p operand tiles in shared memory
 constexpr int kMaxWideP = 256; // streamed tensor-core operators (bounds, Psi^H)
 constexpr int kMaxWideSolveP = 384;  // graph-driven tensor-core solver above kMaxTcP
+constexpr int kMaxWideFwdP = 384;    // tensor-core Gram-block forward (img_psi)
 size_t bounds_smem_bytes(int p);
 
 }  // namespace img

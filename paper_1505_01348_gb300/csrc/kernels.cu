@@ -314,8 +314,8 @@ __global__ void __launch_bounds__(kWideThreads, 1) k_psi_adj_wide(const JobDev *
 // block (m, nb) in that order (-1: not formed).
 struct FwdMap {
     int np;
-    int m[8], nb[8];
-    int idx[4][2];
+    int m[16], nb[16];
+    int idx[6][3];      // 2 Kp <= 768 features: 6 row blocks of 128, 3 column blocks of 256
 };
 
 __global__ void k_fwd_wmax(const float *w, int Q, unsigned *wbits) { fwd_wmax(w, Q, wbits); }
@@ -1537,16 +1537,17 @@ cudaError_t launch_psi(const JobDev *job_dev, const float *wx, float2 *part, int
 }
 
 // Partial blocks (one per CTA, at most one CTA per SM) followed by the
-// summed blocks (at most 6, in doubles).
-size_t psi_wide_part_floats(int sms) { return (size_t)sms * kTcM * 256 + (size_t)2 * 8 * kTcM * 256; }
+// summed blocks (at most 12 at Kp = 384, in doubles; room for 16).
+size_t psi_wide_part_floats(int sms) { return (size_t)sms * kTcM * 256 + (size_t)2 * 16 * kTcM * 256; }
 
 cudaError_t launch_psi_wide(const JobDev *job_dev, unsigned *wbits, const float *wx, float *part, int Q, int p,
                             int n_l, int n_m, int mode, double2 *Kout, cudaStream_t st) {
-    if (p < 1 || p > kMaxWideP || (mode != 1 && mode != 2)) return cudaErrorInvalidValue;
+    if (p < 1 || p > kMaxWideFwdP || (mode != 1 && mode != 2)) return cudaErrorInvalidValue;
+    if (fwd_pairs(p, nullptr, nullptr) > 16) return cudaErrorInvalidValue;
     FwdMap map{};
     map.np = fwd_pairs(p, map.m, map.nb);
-    for (int a = 0; a < 4; ++a)
-        for (int b = 0; b < 2; ++b) map.idx[a][b] = -1;
+    for (int a = 0; a < 6; ++a)
+        for (int b = 0; b < 3; ++b) map.idx[a][b] = -1;
     for (int q = 0; q < map.np; ++q) map.idx[map.m[q]][map.nb[q]] = q;
     const int sms = num_sms();
     const int nblk = fwd_nblocks(n_l, n_m);

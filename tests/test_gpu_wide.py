@@ -6,8 +6,8 @@ chunk; up to p = 256) and the (tile, unit) work-item adjoint (256 < p <=
 * dirty image d_i = a_i^H R a_i and MVDR bound C / (a_i^H R^-1 a_i)
   (Sec. IV-A, Eq. 24), every pixel, ragged tiles and p not a multiple of 8;
 * Psi^H vect(U) = Re diag(A^H U A) (Eq. 16) for a random Hermitian U;
-* Psi x = vect(A diag(x) A^H) (Eq. 15, the tensor-core Gram-block forward)
-  for signed, sparse and wide-range x;
+* Psi x = vect(A diag(x) A^H) (Eq. 15, the tensor-core Gram-block forward,
+  up to 12 blocks at p = 330) for signed, sparse and wide-range x;
 * a solve whose bounds come from this operator (solver on CUDA cores) against
   the oracle image;
 * one batch mixing wide and narrow arrays equals the jobs run one by one.
@@ -72,8 +72,7 @@ def test_wide_psi_adjoint(G, p, prec):
     U = X + X.conj().T
     im = G.Imager.from_job(job, precision=prec)
     y = im.psi_adj(U)
-    # adjoint identity against the forward operator (tensor-core Gram blocks
-    # up to p = 256, CUDA cores above)
+    # adjoint identity against the forward operator (tensor-core Gram blocks)
     x = rng.random(job.Q)
     K = im.psi(x)
     im.close()
@@ -84,7 +83,8 @@ def test_wide_psi_adjoint(G, p, prec):
 
 
 @pytest.mark.parametrize("prec", [1, 2])
-@pytest.mark.parametrize("p,nl,nm", [(65, 21, 13), (96, 24, 20), (128, 16, 16), (200, 17, 11), (256, 20, 12)])
+@pytest.mark.parametrize("p,nl,nm", [(65, 21, 13), (96, 24, 20), (128, 16, 16), (200, 17, 11), (256, 20, 12),
+                                    (288, 15, 13), (330, 9, 14)])
 @pytest.mark.parametrize("kind", ["signed", "sparse", "range"])
 def test_wide_forward(G, p, nl, nm, prec, kind):
     job = synth.custom(900 + p, p, nl, nm, 2, 4 * p + 100, radius=6.0)
